@@ -1,0 +1,95 @@
+"""The seeded input module: design model against the oracle's restatement,
+its Jacobian against finite differences, and the stored FWER thresholds
+against the oracle's own calibration (Eq. 2)."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import design, quad
+
+
+def test_mean_shift_matches_oracle_restatement():
+    for d in [3, 10, 20]:
+        for q in [0.05, 0.3, 0.95]:
+            for dp, dm in [(0.5, 0.1), (0.3, 0.2), (0.8, 0.2)]:
+                mu, _, _ = workloads.design_region(q, 0.5, dp, dm, d, 0.03, 0.0)
+                np.testing.assert_allclose(mu, design.mean_shift(q, dp, dm, d, 211.0), rtol=1e-15, atol=0)
+
+
+def test_jacobian_matches_finite_differences():
+    tab = workloads.tables()["c4"]
+    curve = workloads.ScaleCurve(tab["a"], tab["scale"])
+    theta = np.array([0.37, 0.55, 0.5, 0.1])
+
+    def t_of(th):
+        s, ds = curve(th[1])
+        mu, b, _ = workloads.design_region(th[0], th[1], th[2], th[3], 10, float(s), float(ds))
+        return b - mu
+    s, ds = curve(theta[1])
+    _, _, jac = workloads.design_region(*theta, 10, float(s), float(ds))
+    h = 1e-6
+    for k in range(4):
+        e = np.zeros(4)
+        e[k] = h
+        fd = (t_of(theta + e) - t_of(theta - e)) / (2 * h)
+        np.testing.assert_allclose(jac[:, k], fd, rtol=1e-6, atol=1e-8)
+
+
+@pytest.mark.parametrize("config", ["c2", "c4", "c5"])
+def test_stored_thresholds_satisfy_fwer(config):
+    rng = np.random.default_rng(7)
+    if config == "c2":
+        tab = workloads.tables()["c2"]["scenarios"][3]
+        d, st = 3, {"kind": "equi", "rho": tab["rho"]}
+    elif config == "c4":
+        tab = workloads.tables()["c4"]
+        d, st = 10, {"kind": "ar1", "rho": 0.3}
+    else:
+        tab = workloads.tables()["c5"]
+        d, st = 20, {"kind": "block", "sizes": [5, 5, 5, 5], "rho_in": 0.6, "rho_out": 0.1}
+    curve = workloads.ScaleCurve(tab["a"], tab["scale"])
+    S = quad.structured_sigma(d, st)
+    for a in rng.uniform(0.2, 0.8, 2):
+        s, _ = curve(a)
+        b = quad.thresholds(float(s), workloads.alloc_weights(a, d))
+        assert quad.fwer(b, S, st) == pytest.approx(0.025, abs=1e-10)
+
+
+def test_stored_scale_equals_fresh_oracle_calibration():
+    tab = workloads.tables()
+    st = {"kind": "equi", "rho": 0.5}
+    s = quad.calibrate_scale(np.ones(3) / 3, 0.025, quad.structured_sigma(3, st), st)
+    assert tab["c1"]["scale"] == pytest.approx(s, abs=1e-14)
+    sc = workloads.c2_scenarios(16)
+    for k in [0, 15]:
+        assert tab["c2"]["scenarios"][k]["rho"] == sc[k][2]
+        a = tab["c2"]["scenarios"][k]["a"][40]
+        st = {"kind": "equi", "rho": sc[k][2]}
+        s = quad.calibrate_scale(workloads.alloc_weights(a, 3), 0.025, quad.structured_sigma(3, st), st)
+        assert tab["c2"]["scenarios"][k]["scale"][40] == pytest.approx(s, abs=1e-14)
+
+
+def test_config_shapes():
+    p1 = workloads.c1()
+    assert p1.n_design == 101 and p1.grid == (1, 101) and int(p1.n_draws[0]) == 100_000
+    assert len(set(p1.keys.tolist())) == 1
+    p2 = workloads.c2(n_scen=2, g1=4, g2=5, n_draws=1000)
+    assert p2.n_design == 40 and p2.grid == (4, 5)
+    assert p2.params[7][:2] == (pytest.approx(np.linspace(0.05, 0.95, 4)[1]), pytest.approx(np.linspace(0.2, 0.8, 5)[2]))
+    p4 = workloads.c4(g1=2, g2=3, n_draws=10)
+    assert p4.n_design == 6 and p4.scen_d[0] == 10
+    p3 = workloads.c3(n_scen=8)
+    assert set(p3.scen_d.tolist()) <= set(range(3, 11))
+    assert all(1e5 <= n <= 1e7 for n in p3.n_draws)
+    for S in p3.sigmas:
+        assert np.allclose(np.diag(S), 1.0) and np.linalg.eigvalsh(S).min() > 0
+    assert list(workloads.c5_subsample()) == sorted(set(workloads.c5_subsample()))
+
+
+def test_c1_surface_has_interior_optimum():
+    # the exact success probability over the C1 cutoff grid peaks inside (0.05, 0.95)
+    p1 = workloads.c1()
+    vals = [1.0 - quad.orthant_equi(p1.t(j), 0.5) for j in range(p1.n_design)]
+    k = int(np.argmax(vals))
+    assert 0 < k < 100
+    assert min(vals) > 0.4 and max(vals) < 0.99
