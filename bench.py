@@ -1,0 +1,440 @@
+"""Benchmark of the design-objective engine on one GB300 (or N replicas).
+
+Step = one pass of the whole hot path over the d=3 design grid (16 scenarios
+x 64 cutoff quantiles x 64 allocations, 1e6 draws per design): Cholesky of
+each Sigma, the fused sampling kernel (Philox -> Box-Muller -> L z ->
+indicator -> hit counts, with the likelihood-ratio and sigmoid adjoint sums
+in the same pass), the FP64 finalisation (p, SE, gradients w.r.t. cutoff,
+allocation, delta+, delta-) and the local-quadratic smoothing with argmax.
+
+Prints one JSON line.  `value` is draw-evaluations per second over the whole
+job (all ranks); `roofline` refers to the sampling kernel; `e2e` times the
+same step through the public API with inputs copied from pinned host memory
+and results copied back; `cpu_baseline` times the FP64 oracle on the host.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MC draw-evals/s & % FP32-pipe peak at d=3/10/20; adjoint overhead vs plain"
+UNIT = "draw-evals/s"
+SM_COUNT_NOMINAL = 152
+LANES = 128
+SM_MAX_MHZ = 2070.0
+WORKLOAD = ("d=3 design grid: 16 scenarios x 64 cutoff quantiles x 64 allocation fractions, "
+            "1e6 FP32 draws per design, forward + adjoint (cutoff, allocation, delta+, delta-; "
+            "sigmoid h=1e-2), FP64 finalisation, local-quadratic smoothing + argmax")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sample_kernel_c2_traffic.txt")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2005_10494_gb300", "csrc", f)
+                  for f in ("sample.cuh", "rng.cuh", "mcd_internal.cuh")]
+
+
+# Algorithmic 32-bit operations per draw-evaluation (one design, one draw):
+#   Philox4x32-10: 10 rounds x (2 wide multiplies + 2 three-input xors) per 4
+#   normals -> 10 per normal; uniform map 2 per normal; Box-Muller 8 per pair
+#   (lg2, scale, sqrt, angle fma, sin, cos, 2 products) -> 4 per normal;
+#   transform d(d+1)/2 FMA; indicator d compares + 1 count.
+#   Adjoint adds 2d + 1 (likelihood-ratio sums) and 7d (sigmoid factors).
+def ops_per_draw(d, grad):
+    ops = 16 * d + d * (d + 1) // 2 + d + 1
+    if grad:
+        ops += 2 * d + 1 + 7 * d
+    return ops
+
+
+# FP32 floating-point work per draw-evaluation (FMA = 2): transform d(d+1),
+# Box-Muller 5 per pair; adjoint 2 per LR sum pair and 9 per sigmoid factor.
+def fp32_flops_per_draw(d, grad):
+    f = d * (d + 1) + 5 * d / 2.0
+    if grad:
+        f += 4 * d + 9 * d
+    return f
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the d=10/20, smoothing and C3 lines")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle baseline")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ CPU oracle
+def cpu_oracle_rate(prob, seconds, h=0.01, seed=0):
+    """Time the FP64 oracle (as it stands) on a sample of the workload's designs."""
+    from oracle import mc as omc
+    rng = np.random.default_rng(123)
+    idx = rng.choice(prob.n_design, 64, replace=False)
+    designs = [{"Sigma": prob.sigmas[prob.design_scen[j]], "t": prob.t(j), "key": int(prob.keys[j]),
+                "n_draws": 20_000} for j in idx[:16]]
+    t0 = time.perf_counter()
+    omc.mc_batch(designs, seed, h=h, grad=True)
+    probe = time.perf_counter() - t0
+    per_draw = probe / (16 * 20_000)
+    n = int(max(1000, min(int(prob.n_draws[0]), seconds / per_draw / 64)))
+    designs = [{"Sigma": prob.sigmas[prob.design_scen[j]], "t": prob.t(j), "key": int(prob.keys[j]),
+                "n_draws": n} for j in idx]
+    t0 = time.perf_counter()
+    omc.mc_batch(designs, seed, h=h, grad=True)
+    dt = time.perf_counter() - t0
+    return {"value": 64 * n / dt, "unit": UNIT, "cores": omc.num_threads(), "kind": "oracle",
+            "sample": "64 designs of the d=3 grid x %d draws each, FP64 estimator with adjoint sums "
+                      "(%.1f s)" % (n, dt)}
+
+
+# ------------------------------------------------------------ reference
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import workloads
+    prob = workloads.c2()
+    per_step = max(1.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    from oracle import mc as omc
+    rng = np.random.default_rng(7)
+    idx = rng.choice(prob.n_design, 32, replace=False)
+    probe = [{"Sigma": prob.sigmas[prob.design_scen[j]], "t": prob.t(j), "key": int(prob.keys[j]),
+              "n_draws": 10_000} for j in idx[:8]]
+    t0 = time.perf_counter()
+    omc.mc_batch(probe, 0, h=0.01, grad=True)
+    per_draw = (time.perf_counter() - t0) / 80_000
+    n = int(max(1000, min(1_000_000, per_step / per_draw / 32)))
+    designs = [{"Sigma": prob.sigmas[prob.design_scen[j]], "t": prob.t(j), "key": int(prob.keys[j]),
+                "n_draws": n} for j in idx]
+    for _ in range(args.warmup):
+        omc.mc_batch(designs, 0, h=0.01, grad=True)
+    times = []
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        omc.mc_batch(designs, s + 1, h=0.01, grad=True)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps * 32 * n / total
+    sample = "32 designs of the d=3 grid x %d draws per step, FP64 oracle estimator with adjoint sums" % n
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": omc.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ our arm
+def traffic_record():
+    """DRAM bytes per sampling launch from the committed ncu summary, or None
+    when the kernel sources changed since that capture."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    rec = {}
+    with open(TRAFFIC_FILE) as f:
+        for ln in f:
+            if ":" in ln and not ln.startswith("#"):
+                k, v = ln.split(":", 1)
+                rec[k.strip()] = v.strip()
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    if rec.get("src_sha256") != h.hexdigest():
+        return None
+    try:
+        return float(rec["dram_bytes_per_launch_full"])
+    except (KeyError, ValueError):
+        return None
+
+
+def kernel_rate(pkg, ctx, prob, grad, reps=2, h=0.01):
+    """Draw-evals/s of the sampling kernel alone on one workload (CUDA events)."""
+    import torch
+    dp = pkg.DeviceProblem.from_workload(prob)
+    plan = pkg.Plan(ctx, dp, grad=grad, k=4 if grad else 0, timing=True)
+    jac = torch.as_tensor(prob.jac_packed(), dtype=torch.float64, device="cuda") if grad else None
+    best = 1e30
+    for r in range(reps + 1):
+        if grad:
+            plan.grad(100 + r, jac, h)
+        else:
+            plan.eval(100 + r)
+        ms = plan.kernel_ms()
+        if r > 0:
+            best = min(best, ms)
+    ctx.sync_status()
+    plan.close()
+    return prob.total_draws() / (best / 1e3), best
+
+
+def run_ours(args, rank, world):
+    import torch
+
+    import paper_2005_10494_gb300 as pkg
+    import workloads
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    ctx = pkg.Context(dev.index)
+    prob = workloads.c2()
+    if world > 1:
+        # weak scaling: each rank evaluates its own independent copy of the grid
+        prob.keys = prob.keys + np.uint64(rank * 1_000_003)
+    dp = pkg.DeviceProblem.from_workload(prob)
+    jac = torch.as_tensor(prob.jac_packed(), dtype=torch.float64, device=dev)
+    plan = pkg.Plan(ctx, dp, grad=True, k=4, autotune=True, graph=True, timing=True)
+    S, G1, G2 = prob.n_scen, prob.grid[0], prob.grid[1]
+    stream = torch.cuda.Stream(device=dev)      # capturable stream for the plan's CUDA graph
+    stream.wait_stream(torch.cuda.current_stream())
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(seed):
+        out = plan.grad(seed, jac, 0.01, stream=stream)
+        sm = pkg.mc_smooth_argmax(ctx, out["p"], S, G1, G2, bandwidth=3.0, degree=2, stream=stream)
+        return out, sm
+
+    for w in range(args.warmup):
+        step(1000 + w)
+    ctx.sync_status()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(dev.index)
+    if rank == 0:
+        clocks.start()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kms = []
+    wall0 = time.perf_counter()
+    for s in range(args.steps):
+        flush.fill_(float(s))                 # evict L2 between steps (256 MB > 126 MB L2)
+        ev[s][0].record(stream)
+        step(s)
+        ev[s][1].record(stream)
+        kms.append(plan.kernel_ms())          # waits for this step
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_total = sum(step_ms) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total = float(t.item())
+    clk = clocks.stop() if rank == 0 else None
+    ctx.sync_status()
+
+    draws = prob.total_draws()
+    value = world * args.steps * draws / t_total
+    kernel_ms = statistics.mean(kms)
+    if rank != 0:
+        return
+
+    cfg3 = plan.config(3)
+    ops = ops_per_draw(3, True)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_ops = sm_count * LANES * SM_MAX_MHZ * 1e6
+    achieved = ops * draws / (kernel_ms / 1e3)
+    traffic = traffic_record()
+    fp32 = fp32_flops_per_draw(3, True) * draws / (kernel_ms / 1e3)
+    fp32_peak = sm_count * LANES * 2 * SM_MAX_MHZ * 1e6
+
+    # e2e: same step through the public API from pinned host buffers
+    f64 = torch.float64
+    h_sig = torch.as_tensor(prob.sigma_packed(), dtype=f64).pin_memory()
+    h_mu = torch.as_tensor(prob.mu_packed(), dtype=f64).pin_memory()
+    h_b = torch.as_tensor(prob.b_packed(), dtype=f64).pin_memory()
+    h_jac = torch.as_tensor(prob.jac_packed(), dtype=f64).pin_memory()
+    J = prob.n_design
+    outs_h = {"p": torch.empty(J, dtype=f64).pin_memory(), "hits": torch.empty(J, dtype=torch.int64).pin_memory(),
+              "grad_lr": torch.empty(4 * J, dtype=f64).pin_memory(), "grad_sig": torch.empty(4 * J, dtype=f64).pin_memory(),
+              "grad_se": torch.empty(4 * J, dtype=f64).pin_memory(), "smoothed": torch.empty(J, dtype=f64).pin_memory(),
+              "argmax_idx": torch.empty(S, dtype=torch.int64).pin_memory(),
+              "argmax_val": torch.empty(S, dtype=f64).pin_memory()}
+    h2d = sum(t.numel() * t.element_size() for t in (h_sig, h_mu, h_b, h_jac))
+    d2h = sum(t.numel() * t.element_size() for t in outs_h.values())
+    torch.cuda.synchronize()
+    e2e_times = []
+    for s in range(args.steps):
+        flush.fill_(float(s))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dp.Sigma.copy_(h_sig, non_blocking=True)
+        dp.mu.copy_(h_mu, non_blocking=True)
+        dp.b.copy_(h_b, non_blocking=True)
+        jac.copy_(h_jac, non_blocking=True)
+        out, sm = step(500 + s)
+        for name in ("p", "hits", "grad_lr", "grad_sig", "grad_se"):
+            outs_h[name].copy_(out[name], non_blocking=True)
+        for name in ("smoothed", "argmax_idx", "argmax_val"):
+            outs_h[name].copy_(sm[name], non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_value = world * draws * args.steps / sum(e2e_times)
+
+    extras = {}
+    if not args.no_extras:
+        extras = run_extras(pkg, ctx, prob)
+
+    cpu = cpu_oracle_rate(prob, args.cpu_seconds)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "designs": int(J), "draws_per_design": int(prob.n_draws[0]),
+                   "d": 3, "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "l2": "flushed between steps (256 MB write); inputs and outputs are < 20 MB",
+                   "launch": {"threads": cfg3["threads"], "tile_draws": cfg3["tile_draws"],
+                              "blocks_per_sm": cfg3["blocks_per_sm"], "tiles": plan.tiles(),
+                              "cuda_graph": True, "autotuned": True}},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
+                     "frac": achieved / peak_ops, "traffic": traffic,
+                     "kernel": "sample_kernel<3,3,grad,float>", "kernel_ms": kernel_ms,
+                     "ops_per_draw": ops, "peak_basis": "%d SMs x 128 lanes x %.0f MHz (max SM clock), "
+                     "one 32-bit op per lane per clock" % (sm_count, SM_MAX_MHZ)},
+        "fp32_pipe": {"achieved_tflops": fp32 / 1e12, "peak_tflops": fp32_peak / 1e12, "frac": fp32 / fp32_peak,
+                      "flops_per_draw": fp32_flops_per_draw(3, True)},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        # per step: Cholesky, sampling, finalisation, smoothing weights,
+        # stencil and argmax
+        "gpu_launches": args.steps * 6,
+        "clocks": clk,
+        "wall_s_timed": wall,
+        "cpu_baseline": cpu,
+        "extras": extras,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_extras(pkg, ctx, c2):
+    import torch
+
+    import workloads
+    ex = {}
+    r3f, _ = kernel_rate(pkg, ctx, c2, grad=False)
+    r3g, _ = kernel_rate(pkg, ctx, c2, grad=True)
+    ex["d3"] = {"fwd": r3f, "adj": r3g, "adjoint_overhead": r3f / r3g,
+                "fwd_op_frac": r3f * ops_per_draw(3, False) / (152 * LANES * SM_MAX_MHZ * 1e6)}
+    c4 = workloads.c4()
+    r10f, _ = kernel_rate(pkg, ctx, c4, grad=False, reps=1)
+    r10g, _ = kernel_rate(pkg, ctx, c4, grad=True, reps=1)
+    ex["d10"] = {"fwd": r10f, "adj": r10g, "adjoint_overhead": r10f / r10g,
+                 "fwd_op_frac": r10f * ops_per_draw(10, False) / (152 * LANES * SM_MAX_MHZ * 1e6)}
+    c5 = workloads.c5()
+    r20f, _ = kernel_rate(pkg, ctx, c5, grad=False, reps=1)
+    r20g, _ = kernel_rate(pkg, ctx, c5, grad=True, reps=1)
+    ex["d20"] = {"fwd": r20f, "adj": r20g, "adjoint_overhead": r20f / r20g,
+                 "fwd_op_frac": r20f * ops_per_draw(20, False) / (152 * LANES * SM_MAX_MHZ * 1e6)}
+    # smoothing at scale: 4096 scenarios x 256 x 256 FP64 grids
+    S, G = 4096, 256
+    v = torch.rand(S * G * G, dtype=torch.float64, device="cuda")
+    best = 1e30
+    for r in range(4):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        pkg.mc_smooth_argmax(ctx, v, S, G, G, bandwidth=3.0, degree=2)
+        b.record()
+        b.synchronize()
+        if r > 0:
+            best = min(best, a.elapsed_time(b))
+    ctx.sync_status()
+    nbytes = 16.0 * S * G * G
+    ex["smoothing"] = {"grid": "4096 x 256 x 256 FP64", "ms": best, "GBps": nbytes / (best / 1e3) / 1e9,
+                       "bytes_algorithmic": nbytes}
+    del v
+    torch.cuda.empty_cache()
+    return ex
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    if args.impl == "reference":
+        run_reference(args, rank)
+    else:
+        run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

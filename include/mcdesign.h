@@ -1,0 +1,205 @@
+/*
+ * mcdesign -- Monte Carlo engine for the design objective of biomarker
+ * clinical trials on NVIDIA GB300 (sm_103a).
+ *
+ * The objective (Sec. 2.1, Eq. 4 with a point prior; Eq. 2 at mu = 0) is the
+ * probability that a trial succeeds,
+ *
+ *     p = P(X_i > b_i for some i),   X ~ N(mu, Sigma),  d = dim X <= 20,
+ *
+ * i.e. 1 - Phi_Sigma(b - mu).  The engine estimates p for many designs at
+ * once by the Monte Carlo method of Sec. 2.2 (Eq. 6-7) with independent
+ * draws per design, returns derivatives of p (Appendix A.3 proves p
+ * smooth), and smooths a grid of estimates and takes its argmax (Sec. 2.3).
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns an mcd_status.  Argument errors are found on the
+ *    host and returned at once, before any work is queued.  Errors found by
+ *    kernels (a non-positive-definite Sigma, a NaN input) are written to a
+ *    device status word of the context and returned by mcd_sync_status().
+ *    Nothing aborts the process and no kernel traps.
+ *  - Pointers marked DEVICE are device memory of the context's GPU, owned
+ *    by the caller, and must stay valid until the queued work has run.
+ *    Pointers marked HOST are read during the call only.
+ *  - Work is queued on the given stream (NULL: the legacy default stream)
+ *    and the call returns without waiting for it, except where noted.
+ *  - Determinism: a hit count depends only on (seed, key, draw_begin,
+ *    n_draws, d, t = b - mu); it is bit-identical across runs, plans,
+ *    batchings, tile sizes and chunkings of the draw range.  Gradient sums
+ *    are bit-identical across runs of the same plan.
+ *  - Random numbers: normal number m = n*d + i (draw n of the design, axis
+ *    i) is taken from Philox4x32-10 (Salmon et al., SC'11) call c = m/4,
+ *    output word m%4, counter (c_lo, c_hi, key_lo, key_hi), Philox key
+ *    (seed_lo, seed_hi); word x -> u = (2 floor(x/2^9) + 1) 2^-24; words
+ *    (0,1) and (2,3) are Box-Muller pairs z = sqrt(-2 ln u0) (cos, sin)(2 pi u1).
+ *    Designs with equal keys see identical draws (common random numbers).
+ */
+#ifndef MCDESIGN_H
+#define MCDESIGN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t mcd_status;
+#define MCD_OK            0
+#define MCD_EINVAL        1  /* bad argument (found on the host)                 */
+#define MCD_ENOTSPD       2  /* Sigma of scenario mcd_error_index() is not SPD   */
+#define MCD_ECUDA         3  /* a CUDA runtime call failed (text in last_error)  */
+#define MCD_ENOMEM        5  /* device or host allocation failed                 */
+#define MCD_EUNSUPPORTED  6  /* dimension above MCD_MAX_D, or no sm_103a device  */
+#define MCD_ENAN          7  /* NaN in mu or b of design mcd_error_index()       */
+
+#define MCD_MAX_D 20
+
+/* Region whose probability is estimated. */
+#define MCD_ANY_EXCEEDS 0    /* some X_i > b_i: success, Eq. 4 (1 - Phi_Sigma)  */
+#define MCD_ALL_BELOW   1    /* all X_i <= b_i: the CDF of Eq. 6                 */
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st* mcd_stream;
+
+typedef struct mcd_ctx mcd_ctx;
+typedef struct mcd_plan mcd_plan;
+
+/* A batch of designs.  Scenario s has dimension scen_d[s] and correlation
+ * (or covariance) matrix Sigma_s; design j belongs to scenario
+ * design_scen[j] and has mean shift mu_j and thresholds b_j. */
+typedef struct {
+    int32_t n_scen;               /* S >= 1                                      */
+    int32_t n_design;             /* J >= 0                                      */
+    const int32_t*  scen_d;       /* HOST [S], each 1..MCD_MAX_D                 */
+    const int32_t*  design_scen;  /* HOST [J], each 0..S-1                       */
+    const uint64_t* n_draws;      /* HOST [J], draws N_j (0 allowed: p = 0)      */
+    const uint64_t* draw_begin;   /* HOST [J] first draw index, or NULL for 0;   */
+                                  /*   (draw_begin + n_draws) * d < 2^62          */
+    const uint64_t* key;          /* HOST [J] stream key of each design          */
+    const double*   Sigma;        /* DEVICE: S row-major d_s x d_s blocks, packed */
+                                  /*   in scenario order, symmetric, SPD          */
+    const double*   mu;           /* DEVICE: J blocks of d values, design order  */
+    const double*   b;            /* DEVICE: same layout as mu; +inf drops a test */
+    int32_t region;               /* MCD_ANY_EXCEEDS or MCD_ALL_BELOW            */
+} mcd_problem;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device` (which must be sm_103).  The
+ * context owns a device status word; it allocates nothing else. */
+mcd_status mcd_create(mcd_ctx** ctx, int device);
+void       mcd_destroy(mcd_ctx* ctx);
+/* Text of the last error of this context (never NULL). */
+const char* mcd_last_error(const mcd_ctx* ctx);
+/* Scenario or design index of the last ENOTSPD / ENAN error, else -1. */
+int64_t    mcd_error_index(const mcd_ctx* ctx);
+/* Wait for `stream`, then read and clear the device status word. */
+mcd_status mcd_sync_status(mcd_ctx* ctx, mcd_stream stream);
+
+/* ---- plans: set up once, launch many times ------------------------------ */
+
+#define MCD_PLAN_GRAD      1  /* also allocate the workspace of mcd_plan_grad  */
+#define MCD_PLAN_AUTOTUNE  2  /* time tile shapes on this GPU, keep the fastest */
+#define MCD_PLAN_GRAPH     4  /* replay launches from a captured CUDA graph    */
+#define MCD_PLAN_FP64      8  /* all-FP64 sampling (normals, L z, sums); one d */
+#define MCD_PLAN_TIMING   16  /* record CUDA events around the sampling kernels */
+
+/* Plan a problem.  Reads the HOST arrays (copied), keeps the DEVICE
+ * pointers Sigma, mu, b (their contents are read at each launch), uploads
+ * the tile schedule and allocates the workspace (blocking).  With
+ * MCD_PLAN_AUTOTUNE it runs timing launches on the GPU (blocking).
+ * k: number of design parameters of the Jacobian that mcd_plan_grad takes
+ * (1..8), or 0 for gradients with respect to mu. */
+mcd_status mcd_plan_create(mcd_ctx* ctx, const mcd_problem* prob, int32_t flags,
+                           int32_t k, mcd_plan** plan);
+void       mcd_plan_destroy(mcd_plan* plan);
+
+/* Estimate p for every design (Sec. 2.2, Eq. 7 with independent draws).
+ *   hits[J] (DEVICE, u64, may be NULL): draws in the region, exact;
+ *   p[J]    (DEVICE, may be NULL): hits / N;
+ *   se[J]   (DEVICE, may be NULL): sqrt(p (1 - p) / N), the standard error
+ *           that Eq. 8 bounds by 1 / (2 sqrt N). */
+mcd_status mcd_plan_eval(mcd_plan* plan, uint64_t seed, uint64_t* hits, double* p,
+                         double* se, mcd_stream stream);
+
+/* Estimate p and its derivatives in the same sampling pass.
+ *   dt_dtheta (DEVICE, [J][d][k] row-major per design, or NULL when the plan
+ *     has k = 0): Jacobian of t = b - mu with respect to k design parameters.
+ *   h_sigmoid: bandwidth (in units of X) of the smoothed indicator
+ *     1 - prod_i sigma((b_i - X_i) / h), sigma(u) = 1 / (1 + e^-u); <= 0 skips it.
+ *   grad_lr  [J][k] (or packed like mu when k = 0): likelihood-ratio
+ *     estimate, grad_mu p = Sigma^-1 E[(1_R - p)(X - mu)], chained as
+ *     grad_theta p = -(dt/dtheta)^T grad_mu p (the sign of grad_mu flips
+ *     for MCD_ALL_BELOW);
+ *   grad_sig [J][k] (or like mu): the same derivative of the smoothed
+ *     indicator (pathwise), or untouched when h_sigmoid <= 0;
+ *   grad_se  [J][k] (or like mu): batch-means standard error of grad_lr;
+ *   hits, p as in mcd_plan_eval.  Any output pointer may be NULL. */
+mcd_status mcd_plan_grad(mcd_plan* plan, uint64_t seed, const double* dt_dtheta,
+                         double h_sigmoid, uint64_t* hits, double* p, double* grad_lr,
+                         double* grad_sig, double* grad_se, mcd_stream stream);
+
+/* Launch configuration chosen by the plan for dimension d: threads per
+ * block, draws per tile and resident blocks per SM (for reports). */
+mcd_status mcd_plan_config(const mcd_plan* plan, int32_t d, int32_t* threads,
+                           int64_t* tile_draws, int32_t* blocks_per_sm);
+
+/* Number of tiles in the plan's schedule. */
+int64_t    mcd_plan_tiles(const mcd_plan* plan);
+
+/* For a plan created with MCD_PLAN_TIMING: wait for the last launch and
+ * return the time from the start of its first sampling kernel to the end of
+ * its last one, in milliseconds (CUDA events on the launch stream). */
+mcd_status mcd_plan_kernel_ms(mcd_plan* plan, float* ms);
+
+/* ---- one-shot calls (plan, launch, release) ----------------------------- */
+
+/* Plan, launch and release in one call.  The planning reads the HOST
+ * arrays before returning; the workspace is allocated and freed in stream
+ * order (cudaMallocAsync / cudaFreeAsync).  Not for use under stream capture;
+ * plans are. */
+mcd_status mc_design_eval(mcd_ctx* ctx, const mcd_problem* prob, uint64_t seed,
+                          uint64_t* hits, double* p, double* se, mcd_stream stream);
+
+mcd_status mc_design_grad(mcd_ctx* ctx, const mcd_problem* prob, uint64_t seed,
+                          int32_t k, const double* dt_dtheta, double h_sigmoid,
+                          uint64_t* hits, double* p, double* grad_lr, double* grad_sig,
+                          double* grad_se, mcd_stream stream);
+
+/* ---- smoothing and argmax (Sec. 2.3) ------------------------------------ */
+
+/* Local-polynomial smoothing of n_scen grids of g1 x g2 values (row-major,
+ * scenario-major; a grid with g1 == 1 or g2 == 1 is smoothed along its one
+ * axis), then the argmax per scenario.
+ *   value (DEVICE [S*g1*g2]): the noisy estimates, e.g. p from mcd_plan_eval;
+ *   bandwidth: tricube half-width in grid steps, 1 < bandwidth <= 4 (points
+ *     closer than this get positive weight);  degree: 0, 1 or 2 (2 fits
+ *     {1, x, y, x^2, xy, y^2});  windows are cut at the grid edges and the
+ *     least-squares weights are solved in FP64;
+ *   smoothed (DEVICE [S*g1*g2], may be NULL): smoothed values, applied in
+ *     FP32 from FP64 weights (absolute error below 1e-6 for values in [0,1]);
+ *   argmax_idx / argmax_val (DEVICE [S]): lowest row-major index of the
+ *     largest smoothed value, and that value;
+ *   raw_idx / raw_val (DEVICE [S], may be NULL): the same for the input.
+ * Needs g1, g2 >= 1 and, along each smoothed axis, at least degree + 1
+ * points within every window. */
+mcd_status mc_smooth_argmax(mcd_ctx* ctx, int32_t n_scen, int32_t g1, int32_t g2,
+                            const double* value, double bandwidth, int32_t degree,
+                            double* smoothed, int64_t* argmax_idx, double* argmax_val,
+                            int64_t* raw_idx, double* raw_val, mcd_stream stream);
+
+/* ---- unit-check entry points -------------------------------------------- */
+
+/* Normals m_begin .. m_begin+count-1 of stream (seed, key) exactly as the
+ * sampling kernels make them: FP32 path into z32, FP64 path into z64 and the
+ * raw Philox words of calls m_begin/4 .. (m_begin+count-1)/4 into words
+ * (4 per call).  Any output (DEVICE) may be NULL. */
+mcd_status mcd_debug_normals(mcd_ctx* ctx, uint64_t seed, uint64_t key, uint64_t m_begin,
+                             uint64_t count, float* z32, double* z64, uint32_t* words,
+                             mcd_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MCDESIGN_H */

@@ -1,0 +1,22 @@
+// FP32 sampling kernels, one instantiation per dimension (1,2,3,4,5,6,7,8,9,10).
+#include "sample.cuh"
+
+namespace mcd {
+
+const void* sample_kernel_f32_a(int d, bool grad) {
+    switch (d) {
+        case 1: return grad ? reinterpret_cast<const void*>(&sample_kernel<1, 1, true, float>) : reinterpret_cast<const void*>(&sample_kernel<1, 1, false, float>);
+        case 2: return grad ? reinterpret_cast<const void*>(&sample_kernel<2, 2, true, float>) : reinterpret_cast<const void*>(&sample_kernel<2, 2, false, float>);
+        case 3: return grad ? reinterpret_cast<const void*>(&sample_kernel<3, 3, true, float>) : reinterpret_cast<const void*>(&sample_kernel<3, 3, false, float>);
+        case 4: return grad ? reinterpret_cast<const void*>(&sample_kernel<4, 4, true, float>) : reinterpret_cast<const void*>(&sample_kernel<4, 4, false, float>);
+        case 5: return grad ? reinterpret_cast<const void*>(&sample_kernel<5, 5, true, float>) : reinterpret_cast<const void*>(&sample_kernel<5, 5, false, float>);
+        case 6: return grad ? reinterpret_cast<const void*>(&sample_kernel<6, 6, true, float>) : reinterpret_cast<const void*>(&sample_kernel<6, 6, false, float>);
+        case 7: return grad ? reinterpret_cast<const void*>(&sample_kernel<7, 7, true, float>) : reinterpret_cast<const void*>(&sample_kernel<7, 7, false, float>);
+        case 8: return grad ? reinterpret_cast<const void*>(&sample_kernel<8, 8, true, float>) : reinterpret_cast<const void*>(&sample_kernel<8, 8, false, float>);
+        case 9: return grad ? reinterpret_cast<const void*>(&sample_kernel<9, 9, true, float>) : reinterpret_cast<const void*>(&sample_kernel<9, 9, false, float>);
+        case 10: return grad ? reinterpret_cast<const void*>(&sample_kernel<10, 10, true, float>) : reinterpret_cast<const void*>(&sample_kernel<10, 10, false, float>);
+        default: return nullptr;
+    }
+}
+
+}  // namespace mcd

@@ -1,0 +1,356 @@
+// Local-polynomial smoothing of design-grid estimates and their argmax
+// (Sec. 2.3: smooth the noisy P_hat surface, start the search from its best
+// point; the paper fits thin-plate splines, this engine local polynomials on
+// the regular grid).
+//
+// At grid point (i, j) the smoothed value is beta_0 of the weighted least
+// squares fit of the monomials of (k - i, l - j) up to `degree` with tricube
+// product weights w((k-i)/h) w((l-j)/h), w(u) = (1 - |u|^3)^3, over the window
+// of points with positive weight, cut at the grid edges.  beta_0 is a fixed
+// linear stencil for each pair of edge classes (distance to the low and high
+// edge, capped at the reach R), so the FP64 solve runs once per class pair
+// and the application over the grid is a stencil, HBM-bound, in FP32.
+#include <cfloat>
+#include <cmath>
+#include <cstdint>
+
+#include "mcd_internal.cuh"
+
+namespace mcd {
+
+namespace {
+
+constexpr int kMaxReach = 3;
+constexpr int kMaxTaps = (2 * kMaxReach + 1) * (2 * kMaxReach + 1);
+constexpr int kRowsPerBlock = 32;     // output rows of one block (2-D)
+constexpr int kColsPerBlock = 128;    // output columns of one block (2-D)
+constexpr int kRowsPerThread = 16;
+constexpr int kLine = 512;            // outputs of one block (1-D)
+
+__host__ __device__ inline int reach_of(double bw) {
+    const double f = floor(bw);
+    return (f == bw) ? static_cast<int>(bw) - 1 : static_cast<int>(f);
+}
+
+__device__ inline double tricube(double u) {
+    const double a = fabs(u);
+    if (a >= 1.0) return 0.0;
+    const double c = 1.0 - a * a * a;
+    return c * c * c;
+}
+
+// Monomials of (dx, dy) up to the degree ({1, x, y, x^2, xy, y^2}); 1-D drops y.
+__device__ inline int basis(double dx, double dy, int degree, bool two_d, double* x) {
+    int n = 0;
+    x[n++] = 1.0;
+    if (degree >= 1) { x[n++] = dx; if (two_d) x[n++] = dy; }
+    if (degree >= 2) { x[n++] = dx * dx; if (two_d) { x[n++] = dx * dy; x[n++] = dy * dy; } }
+    return n;
+}
+
+// One thread per class pair: stencil weights w[(dx+R)(2R+1) + (dy+R)] in FP64.
+// Class of a position: lo = min(i, R) points below, hi = min(G-1-i, R) above;
+// class id = lo (R+1) + hi.  1-D grids use only the x axis (classes in x).
+__global__ void weights_kernel(int R, double bw, int degree, bool two_d, int gx, int gy,
+                               double* w64, float* w32, DevStatus* status) {
+    const int ncls = (R + 1) * (R + 1);
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (two_d ? ncls * ncls : ncls)) return;
+    const int cx = two_d ? id / ncls : id, cy = two_d ? id % ncls : 0;
+    const int xlo = cx / (R + 1), xhi = cx % (R + 1);
+    const int ylo = two_d ? cy / (R + 1) : 0, yhi = two_d ? cy % (R + 1) : 0;
+    const int T = 2 * R + 1;
+    double* w = w64 + static_cast<int64_t>(id) * kMaxTaps;
+    float* wf = w32 + static_cast<int64_t>(id) * kMaxTaps;
+    for (int q = 0; q < kMaxTaps; ++q) { w[q] = 0.0; wf[q] = 0.0f; }
+    // classes that no position of this grid has are skipped
+    if (xlo + xhi + 1 > gx || (xlo < R && xhi < R && xlo + xhi + 1 != gx)) return;
+    if (two_d && (ylo + yhi + 1 > gy || (ylo < R && yhi < R && ylo + yhi + 1 != gy))) return;
+    double M[6][6] = {};
+    double x[6];
+    int nb = 0;
+    for (int dx = -xlo; dx <= xhi; ++dx) {
+        for (int dy = -ylo; dy <= yhi; ++dy) {
+            const double W = tricube(dx / bw) * (two_d ? tricube(dy / bw) : 1.0);
+            nb = basis(dx, dy, degree, two_d, x);
+            for (int a = 0; a < nb; ++a)
+                for (int c = 0; c < nb; ++c) M[a][c] += W * x[a] * x[c];
+        }
+    }
+    // u = M^-1 e_0 by Gaussian elimination with partial pivoting
+    double u[6] = {1.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int col = 0; col < nb; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < nb; ++r) if (fabs(M[r][col]) > fabs(M[piv][col])) piv = r;
+        if (!(fabs(M[piv][col]) > 1e-12)) { set_status(status, MCD_EINVAL, id); return; }
+        if (piv != col) {
+            for (int c = 0; c < nb; ++c) { const double tmp = M[col][c]; M[col][c] = M[piv][c]; M[piv][c] = tmp; }
+            const double tu = u[col]; u[col] = u[piv]; u[piv] = tu;
+        }
+        for (int r = 0; r < nb; ++r) {
+            if (r == col) continue;
+            const double f = M[r][col] / M[col][col];
+            if (f == 0.0) continue;
+            for (int c = col; c < nb; ++c) M[r][c] -= f * M[col][c];
+            u[r] -= f * u[col];
+        }
+    }
+    for (int r = 0; r < nb; ++r) u[r] /= M[r][r];
+    for (int dx = -xlo; dx <= xhi; ++dx) {
+        for (int dy = -ylo; dy <= yhi; ++dy) {
+            const double W = tricube(dx / bw) * (two_d ? tricube(dy / bw) : 1.0);
+            basis(dx, dy, degree, two_d, x);
+            double s = 0.0;
+            for (int a = 0; a < nb; ++a) s += x[a] * u[a];
+            const int q = two_d ? (dx + R) * T + (dy + R) : (dx + R);
+            w[q] = W * s;
+            wf[q] = static_cast<float>(W * s);
+        }
+    }
+}
+
+__device__ __forceinline__ int cls(int i, int G, int R) {
+    const int lo = i < R ? i : R;
+    const int hi = (G - 1 - i) < R ? (G - 1 - i) : R;
+    return lo * (R + 1) + hi;
+}
+
+// argmax with the lowest index on ties (NaN never wins)
+__device__ __forceinline__ void amax(double& v, long long& i, double v2, long long i2) {
+    if (i2 < 0) return;
+    if (i < 0 || v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; }
+}
+
+__device__ __forceinline__ void block_amax(double& v, long long& i, double* sv, long long* si) {
+    for (int m = 16; m >= 1; m >>= 1) {
+        const double v2 = __shfl_xor_sync(0xffffffffu, v, m);
+        const long long i2 = __shfl_xor_sync(0xffffffffu, i, m);
+        amax(v, i, v2, i2);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { sv[warp] = v; si[warp] = i; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < static_cast<int>(blockDim.x >> 5); ++w) amax(v, i, sv[w], si[w]);
+    }
+}
+
+// 2-D stencil: block = kRowsPerBlock x kColsPerBlock outputs of one scenario.
+template <int R>
+__global__ void __launch_bounds__(256) smooth2d_kernel(const double* __restrict__ val, int g1, int g2,
+                                                       const float* __restrict__ w32,
+                                                       double* __restrict__ out, double* part_v,
+                                                       long long* part_i, double* rpart_v,
+                                                       long long* rpart_i) {
+    constexpr int T = 2 * R + 1;
+    constexpr int SR = kRowsPerBlock + 2 * R, SC = kColsPerBlock + 2 * R;
+    __shared__ float tile[SR][SC];
+    __shared__ double sv[8];
+    __shared__ long long si[8];
+    const int s = blockIdx.z;
+    const int r0 = blockIdx.y * kRowsPerBlock, c0 = blockIdx.x * kColsPerBlock;
+    const double* V = val + static_cast<int64_t>(s) * g1 * g2;
+    double raw_v = -DBL_MAX;
+    long long raw_i = -1;
+    for (int q = threadIdx.x; q < SR * SC; q += blockDim.x) {
+        const int rr = q / SC, cc = q % SC;
+        const int gr = r0 - R + rr, gc = c0 - R + cc;
+        float x = 0.0f;
+        if (gr >= 0 && gr < g1 && gc >= 0 && gc < g2) {
+            const double dv = V[static_cast<int64_t>(gr) * g2 + gc];
+            x = static_cast<float>(dv);
+            const bool own = rr >= R && rr < R + kRowsPerBlock && cc >= R && cc < R + kColsPerBlock;
+            if (own) amax(raw_v, raw_i, dv, static_cast<long long>(gr) * g2 + gc);
+        }
+        tile[rr][cc] = x;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % kColsPerBlock;
+    const int ty = threadIdx.x / kColsPerBlock;           // 0..1
+    const int c = c0 + tx;
+    double best_v = -DBL_MAX;
+    long long best_i = -1;
+    if (c < g2) {
+        const int ncls = (R + 1) * (R + 1);
+        const int interior = R * (R + 1) + R;             // class with R points on both sides
+        const int ccls = cls(c, g2, R);
+        const bool cin = (ccls == interior);
+        float wi[T * T];                                   // interior stencil, in registers
+#pragma unroll
+        for (int q = 0; q < T * T; ++q) wi[q] = __ldg(&w32[static_cast<int64_t>(interior * ncls + interior) * kMaxTaps + q]);
+        // rolling T x T window over the rows this thread owns
+        float win[T][T];
+        const int rb = ty * kRowsPerThread;
+#pragma unroll
+        for (int dx = 0; dx < T - 1; ++dx)
+#pragma unroll
+            for (int dy = 0; dy < T; ++dy) win[dx + 1][dy] = tile[rb + dx][tx + dy];
+#pragma unroll
+        for (int k = 0; k < kRowsPerThread; ++k) {
+#pragma unroll
+            for (int dx = 0; dx < T - 1; ++dx)
+#pragma unroll
+                for (int dy = 0; dy < T; ++dy) win[dx][dy] = win[dx + 1][dy];
+#pragma unroll
+            for (int dy = 0; dy < T; ++dy) win[T - 1][dy] = tile[rb + k + T - 1][tx + dy];
+            const int r = r0 + rb + k;
+            if (r < g1) {
+                const int rcls = cls(r, g1, R);
+                float acc = 0.0f;
+                if (cin && rcls == interior) {
+#pragma unroll
+                    for (int dx = 0; dx < T; ++dx)
+#pragma unroll
+                        for (int dy = 0; dy < T; ++dy) acc = fmaf(wi[dx * T + dy], win[dx][dy], acc);
+                } else {
+                    const float* w = w32 + static_cast<int64_t>(rcls * ncls + ccls) * kMaxTaps;
+#pragma unroll
+                    for (int dx = 0; dx < T; ++dx)
+#pragma unroll
+                        for (int dy = 0; dy < T; ++dy) acc = fmaf(__ldg(&w[dx * T + dy]), win[dx][dy], acc);
+                }
+                const double o = static_cast<double>(acc);
+                const long long idx = static_cast<long long>(r) * g2 + c;
+                if (out) out[static_cast<int64_t>(s) * g1 * g2 + idx] = o;
+                amax(best_v, best_i, o, idx);
+            }
+        }
+    }
+    const int nb = gridDim.x * gridDim.y;
+    const int b = blockIdx.y * gridDim.x + blockIdx.x;
+    block_amax(best_v, best_i, sv, si);
+    if (threadIdx.x == 0) { part_v[static_cast<int64_t>(s) * nb + b] = best_v; part_i[static_cast<int64_t>(s) * nb + b] = best_i; }
+    __syncthreads();
+    block_amax(raw_v, raw_i, sv, si);
+    if (threadIdx.x == 0) { rpart_v[static_cast<int64_t>(s) * nb + b] = raw_v; rpart_i[static_cast<int64_t>(s) * nb + b] = raw_i; }
+}
+
+// 1-D stencil along a line of n points.
+template <int R>
+__global__ void __launch_bounds__(256) smooth1d_kernel(const double* __restrict__ val, int n,
+                                                       const float* __restrict__ w32,
+                                                       double* __restrict__ out, double* part_v,
+                                                       long long* part_i, double* rpart_v,
+                                                       long long* rpart_i) {
+    constexpr int T = 2 * R + 1;
+    __shared__ float line[kLine + 2 * R];
+    __shared__ double sv[8];
+    __shared__ long long si[8];
+    const int s = blockIdx.y;
+    const int c0 = blockIdx.x * kLine;
+    const double* V = val + static_cast<int64_t>(s) * n;
+    double raw_v = -DBL_MAX;
+    long long raw_i = -1;
+    for (int q = threadIdx.x; q < kLine + 2 * R; q += blockDim.x) {
+        const int g = c0 - R + q;
+        float x = 0.0f;
+        if (g >= 0 && g < n) {
+            const double dv = V[g];
+            x = static_cast<float>(dv);
+            if (q >= R && q < R + kLine) amax(raw_v, raw_i, dv, g);
+        }
+        line[q] = x;
+    }
+    __syncthreads();
+    double best_v = -DBL_MAX;
+    long long best_i = -1;
+    for (int q = threadIdx.x; q < kLine; q += blockDim.x) {
+        const int c = c0 + q;
+        if (c >= n) break;
+        const float* w = w32 + static_cast<int64_t>(cls(c, n, R)) * kMaxTaps;
+        float acc = 0.0f;
+#pragma unroll
+        for (int dx = 0; dx < T; ++dx) acc = fmaf(__ldg(&w[dx]), line[q + dx], acc);
+        const double o = static_cast<double>(acc);
+        if (out) out[static_cast<int64_t>(s) * n + c] = o;
+        amax(best_v, best_i, o, c);
+    }
+    const int nb = gridDim.x;
+    block_amax(best_v, best_i, sv, si);
+    if (threadIdx.x == 0) { part_v[static_cast<int64_t>(s) * nb + blockIdx.x] = best_v; part_i[static_cast<int64_t>(s) * nb + blockIdx.x] = best_i; }
+    __syncthreads();
+    block_amax(raw_v, raw_i, sv, si);
+    if (threadIdx.x == 0) { rpart_v[static_cast<int64_t>(s) * nb + blockIdx.x] = raw_v; rpart_i[static_cast<int64_t>(s) * nb + blockIdx.x] = raw_i; }
+}
+
+// One block per scenario: fold the per-block candidates in index order.
+__global__ void argmax_kernel(int nb, const double* part_v, const long long* part_i,
+                              const double* rpart_v, const long long* rpart_i, int64_t* idx,
+                              double* v, int64_t* ridx, double* rv) {
+    __shared__ double sv[8];
+    __shared__ long long si[8];
+    const int s = blockIdx.x;
+    double bv = -DBL_MAX;
+    long long bi = -1;
+    for (int q = threadIdx.x; q < nb; q += blockDim.x)
+        amax(bv, bi, part_v[static_cast<int64_t>(s) * nb + q], part_i[static_cast<int64_t>(s) * nb + q]);
+    block_amax(bv, bi, sv, si);
+    if (threadIdx.x == 0) { if (idx) idx[s] = bi; if (v) v[s] = bv; }
+    __syncthreads();
+    bv = -DBL_MAX;
+    bi = -1;
+    for (int q = threadIdx.x; q < nb; q += blockDim.x)
+        amax(bv, bi, rpart_v[static_cast<int64_t>(s) * nb + q], rpart_i[static_cast<int64_t>(s) * nb + q]);
+    block_amax(bv, bi, sv, si);
+    if (threadIdx.x == 0) { if (ridx) ridx[s] = bi; if (rv) rv[s] = bv; }
+}
+
+int blocks_per_scen(int g1, int g2) {
+    if (g1 == 1 || g2 == 1) {
+        const int n = g1 * g2;
+        return (n + kLine - 1) / kLine;
+    }
+    return ((g2 + kColsPerBlock - 1) / kColsPerBlock) * ((g1 + kRowsPerBlock - 1) / kRowsPerBlock);
+}
+
+}  // namespace
+
+size_t smooth_weight_count() {
+    const int ncls = (kMaxReach + 1) * (kMaxReach + 1);
+    return static_cast<size_t>(ncls) * ncls * kMaxTaps;
+}
+
+// Per-block argmax candidates: smoothed then raw, n_scen * blocks each.
+size_t smooth_candidate_count(int n_scen, int g1, int g2) {
+    return 2 * static_cast<size_t>(n_scen) * blocks_per_scen(g1, g2);
+}
+
+// wbuf / wbuf32: stencil weights (smooth_weight_count() each); part_val /
+// part_idx: smooth_candidate_count() argmax candidates.
+cudaError_t smooth_argmax(int n_scen, int g1, int g2, const double* value, double bandwidth,
+                          int degree, double* smoothed, int64_t* argmax_idx, double* argmax_val,
+                          int64_t* raw_idx, double* raw_val, double* wbuf, float* wbuf32,
+                          double* part_val, int64_t* part_idx, DevStatus* status, cudaStream_t stream) {
+    const int R = reach_of(bandwidth);
+    const bool two_d = (g1 > 1 && g2 > 1);
+    const int ncls = (R + 1) * (R + 1);
+    const int nw = two_d ? ncls * ncls : ncls;
+    const int gx = two_d ? g1 : g1 * g2;
+    weights_kernel<<<(nw + 63) / 64, 64, 0, stream>>>(R, bandwidth, degree, two_d, gx, g2, wbuf, wbuf32,
+                                                      status);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int nb = blocks_per_scen(g1, g2);
+    double* pv = part_val;
+    long long* pi = reinterpret_cast<long long*>(part_idx);
+    double* rpv = part_val + static_cast<size_t>(n_scen) * nb;
+    long long* rpi = pi + static_cast<size_t>(n_scen) * nb;
+    if (two_d) {
+        dim3 grid((g2 + kColsPerBlock - 1) / kColsPerBlock, (g1 + kRowsPerBlock - 1) / kRowsPerBlock, n_scen);
+        if (R == 1) smooth2d_kernel<1><<<grid, 256, 0, stream>>>(value, g1, g2, wbuf32, smoothed, pv, pi, rpv, rpi);
+        else if (R == 2) smooth2d_kernel<2><<<grid, 256, 0, stream>>>(value, g1, g2, wbuf32, smoothed, pv, pi, rpv, rpi);
+        else smooth2d_kernel<3><<<grid, 256, 0, stream>>>(value, g1, g2, wbuf32, smoothed, pv, pi, rpv, rpi);
+    } else {
+        dim3 grid(nb, n_scen);
+        const int n = g1 * g2;
+        if (R == 1) smooth1d_kernel<1><<<grid, 256, 0, stream>>>(value, n, wbuf32, smoothed, pv, pi, rpv, rpi);
+        else if (R == 2) smooth1d_kernel<2><<<grid, 256, 0, stream>>>(value, n, wbuf32, smoothed, pv, pi, rpv, rpi);
+        else smooth1d_kernel<3><<<grid, 256, 0, stream>>>(value, n, wbuf32, smoothed, pv, pi, rpv, rpi);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    argmax_kernel<<<n_scen, 256, 0, stream>>>(nb, pv, pi, rpv, rpi, argmax_idx, argmax_val, raw_idx, raw_val);
+    return cudaGetLastError();
+}
+
+}  // namespace mcd

@@ -1,0 +1,65 @@
+"""Helpers for the GPU parity tests: run the CUDA path through the C ABI and
+the FP64 oracle on the same seeded inputs."""
+import math
+
+import numpy as np
+
+# Same-stream comparison radius (units of X).  The FP32 path forms z with
+# approximate log2 / sqrt / sin / cos (errors below ~1e-5 for |z| <= 5.8) and
+# y = L z with FP32 FMAs; |y_fp32 - y_exact| stays below ~6e-5 for d <= 20,
+# so a draw's indicator can differ from the FP64 oracle's only if some
+# |y_i - t_i| < EPS32.
+EPS32 = 1e-4
+# The FP64 path differs from the oracle only by the last bits of log / sin / cos.
+EPS64 = 1e-9
+
+
+def run(ctx, prob, seed=0, grad=False, k=0, jac=None, h=0.0, region=0, **plan_kw):
+    import torch
+
+    import paper_2005_10494_gb300 as pkg
+    dp = pkg.DeviceProblem.from_workload(prob, region=region)
+    plan = pkg.Plan(ctx, dp, grad=grad, k=k, **plan_kw)
+    jt = None if jac is None else torch.as_tensor(jac, dtype=torch.float64, device="cuda")
+    # graph replay needs a capturable (non-default) stream
+    stream = torch.cuda.Stream() if plan_kw.get("graph") else None
+    if stream is not None:
+        stream.wait_stream(torch.cuda.current_stream())
+    out = plan.grad(seed, jt, h, stream=stream) if grad else plan.eval(seed, stream=stream)
+    if stream is not None:
+        out = plan.grad(seed, jt, h, stream=stream) if grad else plan.eval(seed, stream=stream)  # replay
+        stream.synchronize()
+    ctx.sync_status()
+    res = {name: t.cpu().numpy() for name, t in out.items()}
+    plan.close()
+    return res
+
+
+def oracle_designs(prob, idx):
+    return [{"Sigma": prob.sigmas[prob.design_scen[j]], "t": prob.t(j), "key": int(prob.keys[j]),
+             "n_draws": int(prob.n_draws[j]), "draw_begin": int(prob.draw_begin[j])} for j in idx]
+
+
+def oracle_same_stream(prob, seed, idx, eps=EPS32, grad=False, h=0.0):
+    from oracle import mc
+    return mc.mc_batch(oracle_designs(prob, idx), seed, eps=eps, grad=grad, h=h)
+
+
+def assert_discordance(gpu_hits, ora, idx):
+    """|hits_gpu - hits_oracle| <= ambiguous draws, design by design."""
+    bad = []
+    for k, j in enumerate(idx):
+        diff = abs(int(gpu_hits[j]) - int(ora["hits"][k]))
+        if diff > int(ora["ambiguous"][k]):
+            bad.append((j, int(gpu_hits[j]), int(ora["hits"][k]), int(ora["ambiguous"][k])))
+    assert not bad, "designs outside the same-stream band: %r" % bad[:10]
+
+
+def band(p_exact, n):
+    return 5.0 * math.sqrt(max(p_exact * (1.0 - p_exact), 0.0) / n) + 1e-7
+
+
+def assert_band(p_gpu, p_exact, n, idx):
+    bad = [(j, float(p_gpu[j]), float(p_exact[k])) for k, j in enumerate(idx)
+           if abs(p_gpu[j] - p_exact[k]) > band(p_exact[k], n if np.isscalar(n) else n[k])]
+    assert not bad, "designs outside 5 SE of the exact value: %r" % bad[:10]
