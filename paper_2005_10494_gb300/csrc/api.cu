@@ -410,6 +410,9 @@ struct LaunchArgs {
 // The whole launch sequence of one evaluation on `stream`.
 mcd_status enqueue(mcd_plan* pl, const LaunchArgs& a, cudaStream_t stream) {
     mcd_ctx* ctx = pl->ctx;
+    if (a.grad && (pl->k > 0) != (a.jac != nullptr))
+        return fail(ctx, MCD_EINVAL, "the Jacobian must be given exactly when the plan has k > 0");
+    if (a.grad && !pl->d_gacc && pl->gacc_len) return fail(ctx, MCD_EINVAL, "plan has no gradient workspace");
     MCD_CUDA(cudaMemsetAsync(pl->d_ticket, 0, sizeof(unsigned int) * std::max<size_t>(1, pl->segs.size()), stream),
              "memset");
     if (pl->J > 0) MCD_CUDA(cudaMemsetAsync(pl->d_hits, 0, sizeof(unsigned long long) * pl->J, stream), "memset");
@@ -554,7 +557,9 @@ mcd_status autotune(mcd_ctx* ctx, const mcd_problem* pr, int32_t flags, int32_t 
                     ctx->tuned[key] = c;
                 }
                 mcd_plan trial;
-                st = plan_build(ctx, pr, flags & ~MCD_PLAN_GRAPH, k, &trial, filt);
+                // timing plans take no Jacobian (k = 0): the finalisation is
+                // the same per-design work either way
+                st = plan_build(ctx, pr, flags & ~(MCD_PLAN_GRAPH | MCD_PLAN_TIMING), 0, &trial, filt);
                 LaunchArgs la;
                 la.grad = grad;
                 la.h = grad ? 0.01 : 0.0;

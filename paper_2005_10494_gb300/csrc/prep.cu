@@ -81,6 +81,7 @@ __global__ void finalize_kernel(const FinalizeParams P, bool grad) {
     const int nout = k > 0 ? k : d;
     const int64_t out_off = k > 0 ? static_cast<int64_t>(j) * k : dr.vec_off;
     const double* J = P.jac ? P.jac + dr.vec_off * k : nullptr;
+    if (k > 0 && !J) return;   // the host rejects this; never dereference a missing Jacobian
 
     double A[kMaxD], B[kMaxD], G[kMaxD];
     for (int i = 0; i < d; ++i) { A[i] = 0.0; B[i] = 0.0; G[i] = 0.0; }

@@ -119,13 +119,20 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
-// Two normals from words (w0, w1).  u0 = 1.m0 - (1 - 2^-24) exactly; the
-// angle is 2 pi u1 - pi = 2 pi (1.m1) - (3 pi - 2 pi 2^-24) in (-pi, pi), where
-// the approximate sine and cosine are most accurate, and
+// Two normals from words (w0, w1).  u0 = 1.m0 - (1 - 2^-24) and v = 1 - u0
+// are exact.  r^2 = -2 ln u0 comes from the hardware log2 except near u0 = 1,
+// where that log's absolute error would dominate the small radius; there
+// (v < 1/16) the series -2 ln(1 - v) = 2 (v + v^2/2 + v^3/3 + v^4/4 + ...)
+// is used, truncated after v^4 (error below 4e-7 in r^2).  The angle is
+// 2 pi u1 - pi = 2 pi (1.m1) - (3 pi - 2 pi 2^-24) in (-pi, pi), where the
+// approximate sine and cosine are most accurate, and
 // (cos, sin)(2 pi u1) = -(cos, sin)(angle).
 __device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float& z0, float& z1) {
-    const float u0 = one_point_m(w0) - 0x1.fffffep-1f;          // exact
-    const float r = sqrt_approx(-1.38629436112f * lg2_approx(u0)); // sqrt(-2 ln u0)
+    const float u0 = one_point_m(w0) - 0x1.fffffep-1f;           // exact
+    const float v = 1.0f - u0;                                     // exact
+    const float ser = v * fmaf(v, fmaf(v, fmaf(v, 0.5f, 0.666666667f), 1.0f), 2.0f);
+    const float lg = -1.38629436112f * lg2_approx(u0);
+    const float r = sqrt_approx(v < 0.0625f ? ser : lg);          // sqrt(-2 ln u0)
     const float ang = fmaf(6.28318530718f, one_point_m(w1), -9.42477758f);
     const float nr = -r;
     z0 = nr * cos_approx(ang);

@@ -44,8 +44,10 @@ def test_normals_match_oracle(ctx):
     e64 = np.abs(z64.cpu().numpy() - ref)
     e32 = np.abs(z32.cpu().numpy().astype(np.float64) - ref)
     assert e64.max() < 1e-13
-    # FP32 path: approximate transcendental functions, |z| <= 5.77
-    assert e32.max() < 2e-5
+    # FP32 path: radius error below 1e-6 (series near u0 = 1, hardware log2
+    # elsewhere), angle error below ~1.3e-6 rad (FP32 angle and approximate
+    # sin / cos) times |r| <= 5.77
+    assert e32.max() < 1.2e-5
     assert e32.mean() < 2e-6
 
 
@@ -195,7 +197,7 @@ def test_gradient_sums_same_stream(ctx):
         # move each sum by at most N * 2e-5
         bound = np.abs(Linv.T).sum(axis=1) * (12.0 * amb + 4.0 * n * 2e-5 + amb * np.abs(ora["B"][k]).max() / n) / n
         np.testing.assert_array_less(np.abs(out["grad_lr"][off:off + d] - g_ref), bound + 1e-9)
-        g_sig_ref = ora["G"][k] / (n * h)
+        g_sig_ref = ora["G"][k] / n          # the oracle's G already carries the 1/h
         np.testing.assert_allclose(out["grad_sig"][off:off + d], g_sig_ref, rtol=2e-3, atol=2e-4)
         off += d
 
