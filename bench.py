@@ -73,6 +73,8 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the d=10/20, smoothing and C3 lines")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle baseline")
+    ap.add_argument("--case", default=None, choices=["c2-small", "c4-small", "c5-small", "smooth"],
+                    help="run a small profiling case (a few launches, no timing) and exit")
     return ap.parse_args()
 
 
@@ -143,15 +145,17 @@ def cpu_oracle_rate(prob, seconds, h=0.01, seed=0):
     omc.mc_batch(designs, seed, h=h, grad=True)
     probe = time.perf_counter() - t0
     per_draw = probe / (16 * 20_000)
-    n = int(max(1000, min(int(prob.n_draws[0]), seconds / per_draw / 64)))
+    n = int(prob.n_draws[0])                                  # full draws per design
+    n_des = int(max(16, min(prob.n_design, round(seconds / per_draw / n / 16) * 16)))
+    idx = rng.choice(prob.n_design, n_des, replace=False)
     designs = [{"Sigma": prob.sigmas[prob.design_scen[j]], "t": prob.t(j), "key": int(prob.keys[j]),
                 "n_draws": n} for j in idx]
     t0 = time.perf_counter()
     omc.mc_batch(designs, seed, h=h, grad=True)
     dt = time.perf_counter() - t0
-    return {"value": 64 * n / dt, "unit": UNIT, "cores": omc.num_threads(), "kind": "oracle",
-            "sample": "64 designs of the d=3 grid x %d draws each, FP64 estimator with adjoint sums "
-                      "(%.1f s)" % (n, dt)}
+    return {"value": n_des * n / dt, "unit": UNIT, "cores": omc.num_threads(), "kind": "oracle",
+            "sample": "%d random designs of the d=3 grid x %d draws each (their full draw count), "
+                      "FP64 estimator with adjoint sums, %.1f s" % (n_des, n, dt)}
 
 
 # ------------------------------------------------------------ reference
@@ -419,8 +423,41 @@ def run_extras(pkg, ctx, c2):
     return ex
 
 
+def run_case(case):
+    """Small cases for profilers: a few launches of one kernel, inputs > L2."""
+    import torch
+
+    import paper_2005_10494_gb300 as pkg
+    import workloads
+    ctx = pkg.Context(0)
+    if case == "smooth":
+        S, G = 512, 256                       # 256 MB in, 256 MB out
+        v = torch.rand(S * G * G, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            pkg.mc_smooth_argmax(ctx, v, S, G, G, bandwidth=3.0, degree=2)
+        ctx.sync_status()
+        return
+    if case == "c2-small":
+        prob = workloads.c2(n_scen=2, g1=8, g2=8, n_draws=1_000_000)
+    elif case == "c4-small":
+        prob = workloads.c4(g1=4, g2=4, n_draws=10_000_000)
+    else:
+        prob = workloads.c5(g1=4, g2=4, n_draws=2_000_000)
+    dp = pkg.DeviceProblem.from_workload(prob)
+    jac = torch.as_tensor(prob.jac_packed(), dtype=torch.float64, device="cuda")
+    fwd = pkg.Plan(ctx, dp)
+    adj = pkg.Plan(ctx, dp, grad=True, k=4)
+    for s in range(2):
+        fwd.eval(s)
+        adj.grad(s, jac, 0.01)
+    ctx.sync_status()
+
+
 def main():
     args = parse_args()
+    if args.case:
+        run_case(args.case)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1:

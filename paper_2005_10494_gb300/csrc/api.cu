@@ -420,7 +420,12 @@ mcd_status enqueue(mcd_plan* pl, const LaunchArgs& a, cudaStream_t stream) {
         MCD_CUDA(cudaMemsetAsync(pl->d_gacc, 0, sizeof(unsigned long long) * pl->gacc_len, stream), "memset");
     MCD_CUDA(launch_cholesky(pl->Sigma, pl->d_sig_off, pl->d_scen_d, pl->d_L_off, pl->S, pl->d_L32, pl->d_L64,
                              pl->d_scen_ok, ctx->d_status, stream), "cholesky launch");
-    if (pl->ev[0]) MCD_CUDA(cudaEventRecord(pl->ev[0], stream), "event record");
+    // under stream capture the timing events must become event-record nodes
+    // of the graph (cudaEventRecordExternal), not capture-internal joins
+    cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+    MCD_CUDA(cudaStreamIsCapturing(stream, &capturing), "cudaStreamIsCapturing");
+    const unsigned ev_flags = capturing == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
+    if (pl->ev[0]) MCD_CUDA(cudaEventRecordWithFlags(pl->ev[0], stream, ev_flags), "event record");
     for (size_t q = 0; q < pl->segs.size(); ++q) {
         const Segment& sg = pl->segs[q];
         if (sg.n_tiles == 0) continue;
@@ -446,7 +451,7 @@ mcd_status enqueue(mcd_plan* pl, const LaunchArgs& a, cudaStream_t stream) {
         MCD_CUDA(launch_sample(sg.d_lo, sg.d_hi, a.grad, pl->fp64, sp, sg.grid, sg.cfg.threads, stream),
                  "sampling launch");
     }
-    if (pl->ev[1]) MCD_CUDA(cudaEventRecord(pl->ev[1], stream), "event record");
+    if (pl->ev[1]) MCD_CUDA(cudaEventRecordWithFlags(pl->ev[1], stream, ev_flags), "event record");
     FinalizeParams fp;
     std::memset(&fp, 0, sizeof(fp));
     fp.designs = pl->d_designs;

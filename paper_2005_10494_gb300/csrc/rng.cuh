@@ -78,9 +78,10 @@ __device__ __forceinline__ uint4 philox_fast(uint32_t call_lo, const Round1& r1,
 }
 
 // ---- FP32 Box-Muller ------------------------------------------------------
-// 1.m in [1, 2) with the 23 high bits of x after the leading 9 are dropped.
+// 1.m in [1, 2) from the 23 high bits of x (x >> 9 has no bit in common with
+// the exponent field, so the sum is the bitwise or; one shift-add).
 __device__ __forceinline__ float one_point_m(uint32_t x) {
-    return __uint_as_float(0x3f800000u | (x >> 9));
+    return __uint_as_float((x >> 9) + 0x3f800000u);
 }
 
 __device__ __forceinline__ float lg2_approx(float x) {
@@ -119,20 +120,19 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
-// Two normals from words (w0, w1).  u0 = 1.m0 - (1 - 2^-24) and v = 1 - u0
-// are exact.  r^2 = -2 ln u0 comes from the hardware log2 except near u0 = 1,
-// where that log's absolute error would dominate the small radius; there
-// (v < 1/16) the series -2 ln(1 - v) = 2 (v + v^2/2 + v^3/3 + v^4/4 + ...)
-// is used, truncated after v^4 (error below 4e-7 in r^2).  The angle is
-// 2 pi u1 - pi = 2 pi (1.m1) - (3 pi - 2 pi 2^-24) in (-pi, pi), where the
-// approximate sine and cosine are most accurate, and
+// Two normals from words (w0, w1).  u0 = 1.m0 - (1 - 2^-24) and
+// 2v = 2 (1 - u0) = fma(-2, u0, 2) are exact.  r^2 = -2 ln u0 comes from the
+// hardware log2, whose absolute error (about 2.2e-7 in r^2) grows into a
+// radius error of 1.1e-7 / r for small r; for 2v < 2^-10 the first term of
+// -2 ln(1 - v) = 2v + v^2 + ... is used instead (error v^2 < 2.4e-7 there).
+// The switch point balances the two, so the radius error stays below 4e-6.  The angle is 2 pi u1 - pi = 2 pi (1.m1) - (3 pi - 2 pi 2^-24)
+// in (-pi, pi), where the approximate sine and cosine are most accurate, and
 // (cos, sin)(2 pi u1) = -(cos, sin)(angle).
 __device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float& z0, float& z1) {
-    const float u0 = one_point_m(w0) - 0x1.fffffep-1f;           // exact
-    const float v = 1.0f - u0;                                     // exact
-    const float ser = v * fmaf(v, fmaf(v, fmaf(v, 0.5f, 0.666666667f), 1.0f), 2.0f);
+    const float u0 = one_point_m(w0) - 0x1.fffffep-1f;             // exact
+    const float two_v = fmaf(-2.0f, u0, 2.0f);                       // exact
     const float lg = -1.38629436112f * lg2_approx(u0);
-    const float r = sqrt_approx(v < 0.0625f ? ser : lg);          // sqrt(-2 ln u0)
+    const float r = sqrt_approx(two_v < 0x1p-10f ? two_v : lg);     // sqrt(-2 ln u0)
     const float ang = fmaf(6.28318530718f, one_point_m(w1), -9.42477758f);
     const float nr = -r;
     z0 = nr * cos_approx(ang);

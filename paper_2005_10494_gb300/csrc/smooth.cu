@@ -10,7 +10,6 @@
 // linear stencil for each pair of edge classes (distance to the low and high
 // edge, capped at the reach R), so the FP64 solve runs once per class pair
 // and the application over the grid is a stencil, HBM-bound, in FP32.
-#include <cfloat>
 #include <cmath>
 #include <cstdint>
 
@@ -115,15 +114,61 @@ __device__ __forceinline__ int cls(int i, int G, int R) {
     return lo * (R + 1) + hi;
 }
 
-// argmax with the lowest index on ties (NaN never wins)
-__device__ __forceinline__ void amax(double& v, long long& i, double v2, long long i2) {
-    if (i2 < 0) return;
-    if (i < 0 || v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; }
+// GB300 has little FP64 throughput, so the stencil keeps FP64 only at its
+// edges: values are converted between FP64 and FP32 and ordered for the
+// argmax with integer operations on their bit patterns.
+
+// FP64 -> FP32, round to nearest even (tiny values flush to zero, large ones
+// become infinite, NaN stays NaN).
+__device__ __forceinline__ float d2f_bits(unsigned long long b) {
+    const unsigned hi = static_cast<unsigned>(b >> 32), lo = static_cast<unsigned>(b);
+    const unsigned sign = hi & 0x80000000u;
+    const int e = static_cast<int>((hi >> 20) & 0x7ffu);
+    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1fffffffu;
+    const unsigned up = (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+    const int ef = e - 1023 + 127;
+    unsigned bits = (static_cast<unsigned>(ef) << 23) + m + up;   // a mantissa carry bumps the exponent
+    if (ef <= 0) bits = 0u;
+    if (ef >= 255 || bits >= 0x7f800000u) bits = 0x7f800000u;
+    if (e == 0x7ff && ((hi & 0xfffffu) | lo)) bits = 0x7fc00000u;
+    return __uint_as_float(sign | bits);
 }
 
-__device__ __forceinline__ void block_amax(double& v, long long& i, double* sv, long long* si) {
+// FP32 -> FP64 bits, exact (FP32 subnormals flush to zero).
+__device__ __forceinline__ unsigned long long f2d_bits(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned long long sign = static_cast<unsigned long long>(u & 0x80000000u) << 32;
+    const unsigned e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    if (e == 0) return sign;
+    const unsigned long long ed = (e == 0xffu) ? 0x7ffull : static_cast<unsigned long long>(e + 1023 - 127);
+    return sign | (ed << 52) | (static_cast<unsigned long long>(m) << 29);
+}
+
+// Monotone map of FP64 bit patterns to unsigned keys (larger value, larger key).
+__device__ __forceinline__ unsigned long long order_key(unsigned long long b) {
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ unsigned long long key_bits(unsigned long long k) {
+    return (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+}
+__device__ __forceinline__ bool nan_bits(unsigned long long b) {
+    return (b & 0x7fffffffffffffffull) > 0x7ff0000000000000ull;
+}
+
+// argmax on keys with the lowest index on ties; index -1 means "none"
+__device__ __forceinline__ void amax(unsigned long long& k, long long& i, unsigned long long k2, long long i2) {
+    if (i2 < 0) return;
+    if (i < 0 || k2 > k || (k2 == k && i2 < i)) { k = k2; i = i2; }
+}
+
+__device__ __forceinline__ void amax_value(unsigned long long& k, long long& i, unsigned long long bits, long long idx) {
+    if (!nan_bits(bits)) amax(k, i, order_key(bits), idx);
+}
+
+__device__ __forceinline__ void block_amax(unsigned long long& v, long long& i, unsigned long long* sv, long long* si) {
     for (int m = 16; m >= 1; m >>= 1) {
-        const double v2 = __shfl_xor_sync(0xffffffffu, v, m);
+        const unsigned long long v2 = __shfl_xor_sync(0xffffffffu, v, m);
         const long long i2 = __shfl_xor_sync(0xffffffffu, i, m);
         amax(v, i, v2, i2);
     }
@@ -137,38 +182,50 @@ __device__ __forceinline__ void block_amax(double& v, long long& i, double* sv, 
 
 // 2-D stencil: block = kRowsPerBlock x kColsPerBlock outputs of one scenario.
 template <int R>
-__global__ void __launch_bounds__(256) smooth2d_kernel(const double* __restrict__ val, int g1, int g2,
+__global__ void __launch_bounds__(256) smooth2d_kernel(const unsigned long long* __restrict__ val, int g1, int g2,
                                                        const float* __restrict__ w32,
-                                                       double* __restrict__ out, double* part_v,
-                                                       long long* part_i, double* rpart_v,
-                                                       long long* rpart_i) {
+                                                       unsigned long long* __restrict__ out,
+                                                       unsigned long long* part_v, long long* part_i,
+                                                       unsigned long long* rpart_v, long long* rpart_i) {
     constexpr int T = 2 * R + 1;
     constexpr int SR = kRowsPerBlock + 2 * R, SC = kColsPerBlock + 2 * R;
     __shared__ float tile[SR][SC];
-    __shared__ double sv[8];
+    __shared__ unsigned long long sv[8];
     __shared__ long long si[8];
     const int s = blockIdx.z;
     const int r0 = blockIdx.y * kRowsPerBlock, c0 = blockIdx.x * kColsPerBlock;
-    const double* V = val + static_cast<int64_t>(s) * g1 * g2;
-    double raw_v = -DBL_MAX;
+    const unsigned long long* V = val + static_cast<int64_t>(s) * g1 * g2;
+    unsigned long long raw_v = 0;
     long long raw_i = -1;
-    for (int q = threadIdx.x; q < SR * SC; q += blockDim.x) {
-        const int rr = q / SC, cc = q % SC;
-        const int gr = r0 - R + rr, gc = c0 - R + cc;
-        float x = 0.0f;
-        if (gr >= 0 && gr < g1 && gc >= 0 && gc < g2) {
-            const double dv = V[static_cast<int64_t>(gr) * g2 + gc];
-            x = static_cast<float>(dv);
-            const bool own = rr >= R && rr < R + kRowsPerBlock && cc >= R && cc < R + kColsPerBlock;
-            if (own) amax(raw_v, raw_i, dv, static_cast<long long>(gr) * g2 + gc);
+    // stage the (rows + halo) x (cols + halo) tile as FP32, eight independent
+    // global loads in flight per thread
+    constexpr int kBatch = 8;
+    for (int q0 = threadIdx.x; q0 < SR * SC; q0 += kBatch * 256) {
+        unsigned long long bits[kBatch];
+        bool inb[kBatch];
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+            const int q = q0 + k * 256;
+            const int rr = q / SC, cc = q % SC;
+            const int gr = r0 - R + rr, gc = c0 - R + cc;
+            inb[k] = q < SR * SC && gr >= 0 && gr < g1 && gc >= 0 && gc < g2;
+            bits[k] = inb[k] ? __ldg(&V[static_cast<int64_t>(gr) * g2 + gc]) : 0ull;
         }
-        tile[rr][cc] = x;
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+            const int q = q0 + k * 256;
+            if (q >= SR * SC) break;
+            const int rr = q / SC, cc = q % SC;
+            const bool own = inb[k] && rr >= R && rr < R + kRowsPerBlock && cc >= R && cc < R + kColsPerBlock;
+            if (own) amax_value(raw_v, raw_i, bits[k], static_cast<long long>(r0 - R + rr) * g2 + (c0 - R + cc));
+            tile[rr][cc] = inb[k] ? d2f_bits(bits[k]) : 0.0f;
+        }
     }
     __syncthreads();
     const int tx = threadIdx.x % kColsPerBlock;
     const int ty = threadIdx.x / kColsPerBlock;           // 0..1
     const int c = c0 + tx;
-    double best_v = -DBL_MAX;
+    unsigned long long best_v = 0;
     long long best_i = -1;
     if (c < g2) {
         const int ncls = (R + 1) * (R + 1);
@@ -209,10 +266,10 @@ __global__ void __launch_bounds__(256) smooth2d_kernel(const double* __restrict_
 #pragma unroll
                         for (int dy = 0; dy < T; ++dy) acc = fmaf(__ldg(&w[dx * T + dy]), win[dx][dy], acc);
                 }
-                const double o = static_cast<double>(acc);
+                const unsigned long long o = f2d_bits(acc);
                 const long long idx = static_cast<long long>(r) * g2 + c;
                 if (out) out[static_cast<int64_t>(s) * g1 * g2 + idx] = o;
-                amax(best_v, best_i, o, idx);
+                amax_value(best_v, best_i, o, idx);
             }
         }
     }
@@ -227,32 +284,32 @@ __global__ void __launch_bounds__(256) smooth2d_kernel(const double* __restrict_
 
 // 1-D stencil along a line of n points.
 template <int R>
-__global__ void __launch_bounds__(256) smooth1d_kernel(const double* __restrict__ val, int n,
+__global__ void __launch_bounds__(256) smooth1d_kernel(const unsigned long long* __restrict__ val, int n,
                                                        const float* __restrict__ w32,
-                                                       double* __restrict__ out, double* part_v,
-                                                       long long* part_i, double* rpart_v,
-                                                       long long* rpart_i) {
+                                                       unsigned long long* __restrict__ out,
+                                                       unsigned long long* part_v, long long* part_i,
+                                                       unsigned long long* rpart_v, long long* rpart_i) {
     constexpr int T = 2 * R + 1;
     __shared__ float line[kLine + 2 * R];
-    __shared__ double sv[8];
+    __shared__ unsigned long long sv[8];
     __shared__ long long si[8];
     const int s = blockIdx.y;
     const int c0 = blockIdx.x * kLine;
-    const double* V = val + static_cast<int64_t>(s) * n;
-    double raw_v = -DBL_MAX;
+    const unsigned long long* V = val + static_cast<int64_t>(s) * n;
+    unsigned long long raw_v = 0;
     long long raw_i = -1;
     for (int q = threadIdx.x; q < kLine + 2 * R; q += blockDim.x) {
         const int g = c0 - R + q;
         float x = 0.0f;
         if (g >= 0 && g < n) {
-            const double dv = V[g];
-            x = static_cast<float>(dv);
-            if (q >= R && q < R + kLine) amax(raw_v, raw_i, dv, g);
+            const unsigned long long bits = __ldg(&V[g]);
+            x = d2f_bits(bits);
+            if (q >= R && q < R + kLine) amax_value(raw_v, raw_i, bits, g);
         }
         line[q] = x;
     }
     __syncthreads();
-    double best_v = -DBL_MAX;
+    unsigned long long best_v = 0;
     long long best_i = -1;
     for (int q = threadIdx.x; q < kLine; q += blockDim.x) {
         const int c = c0 + q;
@@ -261,9 +318,9 @@ __global__ void __launch_bounds__(256) smooth1d_kernel(const double* __restrict_
         float acc = 0.0f;
 #pragma unroll
         for (int dx = 0; dx < T; ++dx) acc = fmaf(__ldg(&w[dx]), line[q + dx], acc);
-        const double o = static_cast<double>(acc);
+        const unsigned long long o = f2d_bits(acc);
         if (out) out[static_cast<int64_t>(s) * n + c] = o;
-        amax(best_v, best_i, o, c);
+        amax_value(best_v, best_i, o, c);
     }
     const int nb = gridDim.x;
     block_amax(best_v, best_i, sv, si);
@@ -274,25 +331,31 @@ __global__ void __launch_bounds__(256) smooth1d_kernel(const double* __restrict_
 }
 
 // One block per scenario: fold the per-block candidates in index order.
-__global__ void argmax_kernel(int nb, const double* part_v, const long long* part_i,
-                              const double* rpart_v, const long long* rpart_i, int64_t* idx,
+__global__ void argmax_kernel(int nb, const unsigned long long* part_v, const long long* part_i,
+                              const unsigned long long* rpart_v, const long long* rpart_i, int64_t* idx,
                               double* v, int64_t* ridx, double* rv) {
-    __shared__ double sv[8];
+    __shared__ unsigned long long sv[8];
     __shared__ long long si[8];
     const int s = blockIdx.x;
-    double bv = -DBL_MAX;
+    unsigned long long bv = 0;
     long long bi = -1;
     for (int q = threadIdx.x; q < nb; q += blockDim.x)
         amax(bv, bi, part_v[static_cast<int64_t>(s) * nb + q], part_i[static_cast<int64_t>(s) * nb + q]);
     block_amax(bv, bi, sv, si);
-    if (threadIdx.x == 0) { if (idx) idx[s] = bi; if (v) v[s] = bv; }
+    if (threadIdx.x == 0) {
+        if (idx) idx[s] = bi;
+        if (v) v[s] = bi >= 0 ? __longlong_as_double(static_cast<long long>(key_bits(bv))) : NAN;
+    }
     __syncthreads();
-    bv = -DBL_MAX;
+    bv = 0;
     bi = -1;
     for (int q = threadIdx.x; q < nb; q += blockDim.x)
         amax(bv, bi, rpart_v[static_cast<int64_t>(s) * nb + q], rpart_i[static_cast<int64_t>(s) * nb + q]);
     block_amax(bv, bi, sv, si);
-    if (threadIdx.x == 0) { if (ridx) ridx[s] = bi; if (rv) rv[s] = bv; }
+    if (threadIdx.x == 0) {
+        if (ridx) ridx[s] = bi;
+        if (rv) rv[s] = bi >= 0 ? __longlong_as_double(static_cast<long long>(key_bits(bv))) : NAN;
+    }
 }
 
 int blocks_per_scen(int g1, int g2) {
@@ -331,21 +394,23 @@ cudaError_t smooth_argmax(int n_scen, int g1, int g2, const double* value, doubl
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int nb = blocks_per_scen(g1, g2);
-    double* pv = part_val;
+    unsigned long long* pv = reinterpret_cast<unsigned long long*>(part_val);
     long long* pi = reinterpret_cast<long long*>(part_idx);
-    double* rpv = part_val + static_cast<size_t>(n_scen) * nb;
+    unsigned long long* rpv = pv + static_cast<size_t>(n_scen) * nb;
     long long* rpi = pi + static_cast<size_t>(n_scen) * nb;
+    const unsigned long long* vb = reinterpret_cast<const unsigned long long*>(value);
+    unsigned long long* ob = reinterpret_cast<unsigned long long*>(smoothed);
     if (two_d) {
         dim3 grid((g2 + kColsPerBlock - 1) / kColsPerBlock, (g1 + kRowsPerBlock - 1) / kRowsPerBlock, n_scen);
-        if (R == 1) smooth2d_kernel<1><<<grid, 256, 0, stream>>>(value, g1, g2, wbuf32, smoothed, pv, pi, rpv, rpi);
-        else if (R == 2) smooth2d_kernel<2><<<grid, 256, 0, stream>>>(value, g1, g2, wbuf32, smoothed, pv, pi, rpv, rpi);
-        else smooth2d_kernel<3><<<grid, 256, 0, stream>>>(value, g1, g2, wbuf32, smoothed, pv, pi, rpv, rpi);
+        if (R == 1) smooth2d_kernel<1><<<grid, 256, 0, stream>>>(vb, g1, g2, wbuf32, ob, pv, pi, rpv, rpi);
+        else if (R == 2) smooth2d_kernel<2><<<grid, 256, 0, stream>>>(vb, g1, g2, wbuf32, ob, pv, pi, rpv, rpi);
+        else smooth2d_kernel<3><<<grid, 256, 0, stream>>>(vb, g1, g2, wbuf32, ob, pv, pi, rpv, rpi);
     } else {
         dim3 grid(nb, n_scen);
         const int n = g1 * g2;
-        if (R == 1) smooth1d_kernel<1><<<grid, 256, 0, stream>>>(value, n, wbuf32, smoothed, pv, pi, rpv, rpi);
-        else if (R == 2) smooth1d_kernel<2><<<grid, 256, 0, stream>>>(value, n, wbuf32, smoothed, pv, pi, rpv, rpi);
-        else smooth1d_kernel<3><<<grid, 256, 0, stream>>>(value, n, wbuf32, smoothed, pv, pi, rpv, rpi);
+        if (R == 1) smooth1d_kernel<1><<<grid, 256, 0, stream>>>(vb, n, wbuf32, ob, pv, pi, rpv, rpi);
+        else if (R == 2) smooth1d_kernel<2><<<grid, 256, 0, stream>>>(vb, n, wbuf32, ob, pv, pi, rpv, rpi);
+        else smooth1d_kernel<3><<<grid, 256, 0, stream>>>(vb, n, wbuf32, ob, pv, pi, rpv, rpi);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -44,7 +44,7 @@ def test_normals_match_oracle(ctx):
     e64 = np.abs(z64.cpu().numpy() - ref)
     e32 = np.abs(z32.cpu().numpy().astype(np.float64) - ref)
     assert e64.max() < 1e-13
-    # FP32 path: radius error below 1e-6 (series near u0 = 1, hardware log2
+    # FP32 path: radius error below 4e-6 (2v near u0 = 1, hardware log2
     # elsewhere), angle error below ~1.3e-6 rad (FP32 angle and approximate
     # sin / cos) times |r| <= 5.77
     assert e32.max() < 1.2e-5
@@ -89,6 +89,27 @@ def test_reruns_are_bit_identical(ctx):
     np.testing.assert_array_equal(a["hits"], c["hits"])
     d = run(ctx, prob, seed=10)
     assert not np.array_equal(a["hits"], d["hits"])
+
+
+def test_graph_replay_with_timing(ctx):
+    import torch
+
+    import paper_2005_10494_gb300 as pkg
+    prob = workloads.c2(n_scen=1, g1=4, g2=4, n_draws=200_000)
+    dp = pkg.DeviceProblem.from_workload(prob)
+    jac = torch.as_tensor(prob.jac_packed(), dtype=torch.float64, device="cuda")
+    plain = pkg.Plan(ctx, dp, grad=True, k=4)
+    ref = {k: v.cpu().numpy() for k, v in plain.grad(5, jac, 0.01).items()}
+    plan = pkg.Plan(ctx, dp, grad=True, k=4, graph=True, timing=True)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    for seed in (4, 5, 5):                     # capture, re-capture on a new seed, replay
+        out = plan.grad(seed, jac, 0.01, stream=s)
+        assert plan.kernel_ms() > 0.0
+    s.synchronize()
+    ctx.sync_status()
+    for k in ref:
+        np.testing.assert_array_equal(out[k].cpu().numpy(), ref[k])
 
 
 def test_one_shot_equals_plan(ctx):
