@@ -176,11 +176,13 @@ class DeviceProblem:
 
 
 def _outputs(J, vec_len, k, grad, device, want_sig):
+    """Output buffers of one call kind: exactly the arrays that call writes."""
     torch = _torch()
     out = {"hits": torch.empty(max(J, 1), dtype=torch.int64, device=device),
-           "p": torch.empty(max(J, 1), dtype=torch.float64, device=device),
-           "se": torch.empty(max(J, 1), dtype=torch.float64, device=device)}
-    if grad:
+           "p": torch.empty(max(J, 1), dtype=torch.float64, device=device)}
+    if not grad:
+        out["se"] = torch.empty(max(J, 1), dtype=torch.float64, device=device)
+    else:
         n = J * k if k > 0 else vec_len
         out["grad_lr"] = torch.empty(max(n, 1), dtype=torch.float64, device=device)
         out["grad_se"] = torch.empty(max(n, 1), dtype=torch.float64, device=device)
