@@ -326,8 +326,9 @@ struct Dispatch {
     }
 };
 
+// The persistent loop over tiles (the body of both kernel wrappers below).
 template <int DLO, int DHI, bool GRAD, typename R>
-__global__ void __launch_bounds__(256) sample_kernel(const __grid_constant__ SampleParams P) {
+__device__ __forceinline__ void sample_body(const SampleParams& P) {
     __shared__ TileShared<R> ts;
     __shared__ uint32_t cred[kMaxWarps];
     __shared__ R gred[kMaxWarps][GRAD ? 3 * DHI : 1];
@@ -377,6 +378,19 @@ __global__ void __launch_bounds__(256) sample_kernel(const __grid_constant__ Sam
         if (ts.ok) Dispatch<DLO, DHI, GRAD, R>::run(d, ts, P, cred, gred);
         __syncthreads();
     }
+}
+
+template <int DLO, int DHI, bool GRAD, typename R>
+__global__ void __launch_bounds__(256) sample_kernel(const __grid_constant__ SampleParams P) {
+    sample_body<DLO, DHI, GRAD, R>(P);
+}
+
+// Adjoint kernels of larger d carry 3d accumulators per thread; this variant
+// asks the compiler for two resident 256-thread blocks (<= 128 registers) so
+// that an SM keeps 16 warps to hide the Philox and MUFU latencies.
+template <int DLO, int DHI, bool GRAD, typename R>
+__global__ void __launch_bounds__(256, 2) sample_kernel_2b(const __grid_constant__ SampleParams P) {
+    sample_body<DLO, DHI, GRAD, R>(P);
 }
 
 }  // namespace mcd

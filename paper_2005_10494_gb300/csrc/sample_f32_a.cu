@@ -1,4 +1,5 @@
 // FP32 sampling kernels, one instantiation per dimension (1,2,3,4,5,6,7,8,9,10).
+// Adjoint kernels of d >= 7 use the two-blocks-per-SM register bound.
 #include "sample.cuh"
 
 namespace mcd {
@@ -11,10 +12,10 @@ const void* sample_kernel_f32_a(int d, bool grad) {
         case 4: return grad ? reinterpret_cast<const void*>(&sample_kernel<4, 4, true, float>) : reinterpret_cast<const void*>(&sample_kernel<4, 4, false, float>);
         case 5: return grad ? reinterpret_cast<const void*>(&sample_kernel<5, 5, true, float>) : reinterpret_cast<const void*>(&sample_kernel<5, 5, false, float>);
         case 6: return grad ? reinterpret_cast<const void*>(&sample_kernel<6, 6, true, float>) : reinterpret_cast<const void*>(&sample_kernel<6, 6, false, float>);
-        case 7: return grad ? reinterpret_cast<const void*>(&sample_kernel<7, 7, true, float>) : reinterpret_cast<const void*>(&sample_kernel<7, 7, false, float>);
-        case 8: return grad ? reinterpret_cast<const void*>(&sample_kernel<8, 8, true, float>) : reinterpret_cast<const void*>(&sample_kernel<8, 8, false, float>);
-        case 9: return grad ? reinterpret_cast<const void*>(&sample_kernel<9, 9, true, float>) : reinterpret_cast<const void*>(&sample_kernel<9, 9, false, float>);
-        case 10: return grad ? reinterpret_cast<const void*>(&sample_kernel<10, 10, true, float>) : reinterpret_cast<const void*>(&sample_kernel<10, 10, false, float>);
+        case 7: return grad ? reinterpret_cast<const void*>(&sample_kernel_2b<7, 7, true, float>) : reinterpret_cast<const void*>(&sample_kernel<7, 7, false, float>);
+        case 8: return grad ? reinterpret_cast<const void*>(&sample_kernel_2b<8, 8, true, float>) : reinterpret_cast<const void*>(&sample_kernel<8, 8, false, float>);
+        case 9: return grad ? reinterpret_cast<const void*>(&sample_kernel_2b<9, 9, true, float>) : reinterpret_cast<const void*>(&sample_kernel<9, 9, false, float>);
+        case 10: return grad ? reinterpret_cast<const void*>(&sample_kernel_2b<10, 10, true, float>) : reinterpret_cast<const void*>(&sample_kernel<10, 10, false, float>);
         default: return nullptr;
     }
 }

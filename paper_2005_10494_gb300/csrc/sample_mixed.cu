@@ -5,7 +5,7 @@
 namespace mcd {
 
 const void* sample_kernel_mixed(bool grad) {
-    return grad ? reinterpret_cast<const void*>(&sample_kernel<1, kMixedMaxD, true, float>)
+    return grad ? reinterpret_cast<const void*>(&sample_kernel_2b<1, kMixedMaxD, true, float>)
                 : reinterpret_cast<const void*>(&sample_kernel<1, kMixedMaxD, false, float>);
 }
 

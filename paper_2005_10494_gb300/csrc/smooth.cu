@@ -118,31 +118,29 @@ __device__ __forceinline__ int cls(int i, int G, int R) {
 // edges: values are converted between FP64 and FP32 and ordered for the
 // argmax with integer operations on their bit patterns.
 
-// FP64 -> FP32, round to nearest even (tiny values flush to zero, large ones
-// become infinite, NaN stays NaN).
+// FP64 -> FP32 with rounding of the dropped bits half-up (error at most half
+// an FP32 ulp); magnitudes below the FP32 normal range become 0, above it
+// infinity, NaN stays NaN.  The mantissa and exponent move together with one
+// funnel shift: (hi:lo) << 3 puts the low 8 exponent bits and the top 23
+// mantissa bits in place, and subtracting (1023 - 127) << 23 rebiases.
 __device__ __forceinline__ float d2f_bits(unsigned long long b) {
     const unsigned hi = static_cast<unsigned>(b >> 32), lo = static_cast<unsigned>(b);
-    const unsigned sign = hi & 0x80000000u;
-    const int e = static_cast<int>((hi >> 20) & 0x7ffu);
-    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
-    const unsigned rest = lo & 0x1fffffffu;
-    const unsigned up = (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
-    const int ef = e - 1023 + 127;
-    unsigned bits = (static_cast<unsigned>(ef) << 23) + m + up;   // a mantissa carry bumps the exponent
-    if (ef <= 0) bits = 0u;
-    if (ef >= 255 || bits >= 0x7f800000u) bits = 0x7f800000u;
-    if (e == 0x7ff && ((hi & 0xfffffu) | lo)) bits = 0x7fc00000u;
-    return __uint_as_float(sign | bits);
+    const unsigned e = (hi >> 20) & 0x7ffu;
+    unsigned mag = __funnelshift_l(lo, hi, 3) - (896u << 23);
+    mag += (lo >> 28) & 1u;                                   // round half up (carry may reach the exponent)
+    if (e <= 896u) mag = 0u;
+    if (e >= 1151u) mag = (e == 0x7ffu && ((hi & 0xfffffu) | lo)) ? 0x7fc00000u : 0x7f800000u;
+    return __uint_as_float((hi & 0x80000000u) | mag);
 }
 
 // FP32 -> FP64 bits, exact (FP32 subnormals flush to zero).
 __device__ __forceinline__ unsigned long long f2d_bits(float f) {
     const unsigned u = __float_as_uint(f);
-    const unsigned long long sign = static_cast<unsigned long long>(u & 0x80000000u) << 32;
-    const unsigned e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
-    if (e == 0) return sign;
-    const unsigned long long ed = (e == 0xffu) ? 0x7ffull : static_cast<unsigned long long>(e + 1023 - 127);
-    return sign | (ed << 52) | (static_cast<unsigned long long>(m) << 29);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u) return static_cast<unsigned long long>(u & 0x80000000u) << 32;
+    const unsigned hi = (u & 0x80000000u) | (e == 0xffu ? (0x7ffu << 20) | ((u >> 3) & 0xfffffu)
+                                                         : ((u & 0x7fffffffu) >> 3) + (896u << 20));
+    return (static_cast<unsigned long long>(hi) << 32) | (u << 29);
 }
 
 // Monotone map of FP64 bit patterns to unsigned keys (larger value, larger key).
@@ -180,7 +178,29 @@ __device__ __forceinline__ void block_amax(unsigned long long& v, long long& i, 
     }
 }
 
+// Exact running argmax of FP64 values visited in increasing index order: a
+// cheap FP32 comparison first (rounding to FP32 is monotone, so a strictly
+// larger FP32 value means a larger FP64 value and a smaller one a smaller),
+// the exact key comparison only when the FP32 values tie.
+struct RunMax {
+    float f;
+    unsigned long long key;
+    long long idx;
+    __device__ __forceinline__ void init() { f = -INFINITY; key = 0; idx = -1; }
+    __device__ __forceinline__ void add(float x, unsigned long long bits, long long i) {
+        if (x > f) {
+            f = x; key = order_key(bits); idx = i;
+        } else if (x == f && !nan_bits(bits)) {
+            const unsigned long long k = order_key(bits);
+            if (idx < 0 || k > key) { key = k; idx = i; }
+        }
+    }
+};
+
 // 2-D stencil: block = kRowsPerBlock x kColsPerBlock outputs of one scenario.
+// Staging: warp w copies tile rows w, w+8, ... (lanes along the row, no
+// index division), converting FP64 to FP32; then each thread slides a
+// (2R+1) x (2R+1) register window down kRowsPerThread rows of one column.
 template <int R>
 __global__ void __launch_bounds__(256) smooth2d_kernel(const unsigned long long* __restrict__ val, int g1, int g2,
                                                        const float* __restrict__ w32,
@@ -189,43 +209,44 @@ __global__ void __launch_bounds__(256) smooth2d_kernel(const unsigned long long*
                                                        unsigned long long* rpart_v, long long* rpart_i) {
     constexpr int T = 2 * R + 1;
     constexpr int SR = kRowsPerBlock + 2 * R, SC = kColsPerBlock + 2 * R;
+    constexpr int CPL = (SC + 31) / 32;                     // row chunks per lane
     __shared__ float tile[SR][SC];
     __shared__ unsigned long long sv[8];
     __shared__ long long si[8];
     const int s = blockIdx.z;
     const int r0 = blockIdx.y * kRowsPerBlock, c0 = blockIdx.x * kColsPerBlock;
     const unsigned long long* V = val + static_cast<int64_t>(s) * g1 * g2;
-    unsigned long long raw_v = 0;
-    long long raw_i = -1;
-    // stage the (rows + halo) x (cols + halo) tile as FP32, eight independent
-    // global loads in flight per thread
-    constexpr int kBatch = 8;
-    for (int q0 = threadIdx.x; q0 < SR * SC; q0 += kBatch * 256) {
-        unsigned long long bits[kBatch];
-        bool inb[kBatch];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    RunMax raw;
+    raw.init();
+    for (int rr = warp; rr < SR; rr += 8) {
+        const int gr = r0 - R + rr;
+        const bool row_in = gr >= 0 && gr < g1;
+        const bool row_own = rr >= R && rr < R + kRowsPerBlock;
+        const unsigned long long* rowp = V + static_cast<int64_t>(gr) * g2;
+        unsigned long long bits[CPL];
 #pragma unroll
-        for (int k = 0; k < kBatch; ++k) {
-            const int q = q0 + k * 256;
-            const int rr = q / SC, cc = q % SC;
-            const int gr = r0 - R + rr, gc = c0 - R + cc;
-            inb[k] = q < SR * SC && gr >= 0 && gr < g1 && gc >= 0 && gc < g2;
-            bits[k] = inb[k] ? __ldg(&V[static_cast<int64_t>(gr) * g2 + gc]) : 0ull;
+        for (int k = 0; k < CPL; ++k) {
+            const int cc = lane + 32 * k, gc = c0 - R + cc;
+            bits[k] = (row_in && cc < SC && gc >= 0 && gc < g2) ? __ldg(rowp + gc) : 0ull;
         }
 #pragma unroll
-        for (int k = 0; k < kBatch; ++k) {
-            const int q = q0 + k * 256;
-            if (q >= SR * SC) break;
-            const int rr = q / SC, cc = q % SC;
-            const bool own = inb[k] && rr >= R && rr < R + kRowsPerBlock && cc >= R && cc < R + kColsPerBlock;
-            if (own) amax_value(raw_v, raw_i, bits[k], static_cast<long long>(r0 - R + rr) * g2 + (c0 - R + cc));
-            tile[rr][cc] = inb[k] ? d2f_bits(bits[k]) : 0.0f;
+        for (int k = 0; k < CPL; ++k) {
+            const int cc = lane + 32 * k, gc = c0 - R + cc;
+            if (cc < SC) {
+                const bool in = row_in && gc >= 0 && gc < g2;
+                const float x = in ? d2f_bits(bits[k]) : 0.0f;
+                if (in && row_own && cc >= R && cc < R + kColsPerBlock)
+                    raw.add(x, bits[k], static_cast<long long>(gr) * g2 + gc);
+                tile[rr][cc] = x;
+            }
         }
     }
     __syncthreads();
     const int tx = threadIdx.x % kColsPerBlock;
     const int ty = threadIdx.x / kColsPerBlock;           // 0..1
     const int c = c0 + tx;
-    unsigned long long best_v = 0;
+    float best = -INFINITY;
     long long best_i = -1;
     if (c < g2) {
         const int ncls = (R + 1) * (R + 1);
@@ -235,13 +256,13 @@ __global__ void __launch_bounds__(256) smooth2d_kernel(const unsigned long long*
         float wi[T * T];                                   // interior stencil, in registers
 #pragma unroll
         for (int q = 0; q < T * T; ++q) wi[q] = __ldg(&w32[static_cast<int64_t>(interior * ncls + interior) * kMaxTaps + q]);
-        // rolling T x T window over the rows this thread owns
         float win[T][T];
         const int rb = ty * kRowsPerThread;
 #pragma unroll
         for (int dx = 0; dx < T - 1; ++dx)
 #pragma unroll
             for (int dy = 0; dy < T; ++dy) win[dx + 1][dy] = tile[rb + dx][tx + dy];
+        unsigned long long* orow = out ? out + static_cast<int64_t>(s) * g1 * g2 + c : nullptr;
 #pragma unroll
         for (int k = 0; k < kRowsPerThread; ++k) {
 #pragma unroll
@@ -252,34 +273,36 @@ __global__ void __launch_bounds__(256) smooth2d_kernel(const unsigned long long*
             for (int dy = 0; dy < T; ++dy) win[T - 1][dy] = tile[rb + k + T - 1][tx + dy];
             const int r = r0 + rb + k;
             if (r < g1) {
-                const int rcls = cls(r, g1, R);
                 float acc = 0.0f;
-                if (cin && rcls == interior) {
+                const bool rin = (r >= R) && (r <= g1 - 1 - R);
+                if (cin && rin) {
 #pragma unroll
                     for (int dx = 0; dx < T; ++dx)
 #pragma unroll
                         for (int dy = 0; dy < T; ++dy) acc = fmaf(wi[dx * T + dy], win[dx][dy], acc);
                 } else {
-                    const float* w = w32 + static_cast<int64_t>(rcls * ncls + ccls) * kMaxTaps;
+                    const float* w = w32 + static_cast<int64_t>(cls(r, g1, R) * ncls + ccls) * kMaxTaps;
 #pragma unroll
                     for (int dx = 0; dx < T; ++dx)
 #pragma unroll
                         for (int dy = 0; dy < T; ++dy) acc = fmaf(__ldg(&w[dx * T + dy]), win[dx][dy], acc);
                 }
-                const unsigned long long o = f2d_bits(acc);
-                const long long idx = static_cast<long long>(r) * g2 + c;
-                if (out) out[static_cast<int64_t>(s) * g1 * g2 + idx] = o;
-                amax_value(best_v, best_i, o, idx);
+                if (orow) orow[static_cast<int64_t>(r) * g2] = f2d_bits(acc);
+                // rows of this thread come in increasing index order: strict > keeps the lowest
+                if (acc > best) { best = acc; best_i = static_cast<long long>(r) * g2 + c; }
             }
         }
     }
+    unsigned long long best_k = best_i >= 0 ? order_key(f2d_bits(best)) : 0ull;
     const int nb = gridDim.x * gridDim.y;
     const int b = blockIdx.y * gridDim.x + blockIdx.x;
-    block_amax(best_v, best_i, sv, si);
-    if (threadIdx.x == 0) { part_v[static_cast<int64_t>(s) * nb + b] = best_v; part_i[static_cast<int64_t>(s) * nb + b] = best_i; }
+    block_amax(best_k, best_i, sv, si);
+    if (threadIdx.x == 0) { part_v[static_cast<int64_t>(s) * nb + b] = best_k; part_i[static_cast<int64_t>(s) * nb + b] = best_i; }
     __syncthreads();
-    block_amax(raw_v, raw_i, sv, si);
-    if (threadIdx.x == 0) { rpart_v[static_cast<int64_t>(s) * nb + b] = raw_v; rpart_i[static_cast<int64_t>(s) * nb + b] = raw_i; }
+    unsigned long long raw_k = raw.key;
+    long long raw_i = raw.idx;
+    block_amax(raw_k, raw_i, sv, si);
+    if (threadIdx.x == 0) { rpart_v[static_cast<int64_t>(s) * nb + b] = raw_k; rpart_i[static_cast<int64_t>(s) * nb + b] = raw_i; }
 }
 
 // 1-D stencil along a line of n points.
