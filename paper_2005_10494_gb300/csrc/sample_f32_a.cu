@@ -1,5 +1,6 @@
 // FP32 sampling kernels, one instantiation per dimension (1,2,3,4,5,6,7,8,9,10).
-// Adjoint kernels of d >= 7 use the two-blocks-per-SM register bound.
+// Adjoint kernels of d in 7..12 use the two-blocks-per-SM register bound
+// (measured faster there; at larger d the unbounded kernel is faster).
 #include "sample.cuh"
 
 namespace mcd {

@@ -1,5 +1,6 @@
 // FP32 sampling kernels, one instantiation per dimension (11,12,13,14,15,16,17,18,19,20).
-// Adjoint kernels of d >= 7 use the two-blocks-per-SM register bound.
+// Adjoint kernels of d in 7..12 use the two-blocks-per-SM register bound
+// (measured faster there; at larger d the unbounded kernel is faster).
 #include "sample.cuh"
 
 namespace mcd {
@@ -8,14 +9,14 @@ const void* sample_kernel_f32_b(int d, bool grad) {
     switch (d) {
         case 11: return grad ? reinterpret_cast<const void*>(&sample_kernel_2b<11, 11, true, float>) : reinterpret_cast<const void*>(&sample_kernel<11, 11, false, float>);
         case 12: return grad ? reinterpret_cast<const void*>(&sample_kernel_2b<12, 12, true, float>) : reinterpret_cast<const void*>(&sample_kernel<12, 12, false, float>);
-        case 13: return grad ? reinterpret_cast<const void*>(&sample_kernel_2b<13, 13, true, float>) : reinterpret_cast<const void*>(&sample_kernel<13, 13, false, float>);
-        case 14: return grad ? reinterpret_cast<const void*>(&sample_kernel_2b<14, 14, true, float>) : reinterpret_cast<const void*>(&sample_kernel<14, 14, false, float>);
-        case 15: return grad ? reinterpret_cast<const void*>(&sample_kernel_2b<15, 15, true, float>) : reinterpret_cast<const void*>(&sample_kernel<15, 15, false, float>);
-        case 16: return grad ? reinterpret_cast<const void*>(&sample_kernel_2b<16, 16, true, float>) : reinterpret_cast<const void*>(&sample_kernel<16, 16, false, float>);
-        case 17: return grad ? reinterpret_cast<const void*>(&sample_kernel_2b<17, 17, true, float>) : reinterpret_cast<const void*>(&sample_kernel<17, 17, false, float>);
-        case 18: return grad ? reinterpret_cast<const void*>(&sample_kernel_2b<18, 18, true, float>) : reinterpret_cast<const void*>(&sample_kernel<18, 18, false, float>);
-        case 19: return grad ? reinterpret_cast<const void*>(&sample_kernel_2b<19, 19, true, float>) : reinterpret_cast<const void*>(&sample_kernel<19, 19, false, float>);
-        case 20: return grad ? reinterpret_cast<const void*>(&sample_kernel_2b<20, 20, true, float>) : reinterpret_cast<const void*>(&sample_kernel<20, 20, false, float>);
+        case 13: return grad ? reinterpret_cast<const void*>(&sample_kernel<13, 13, true, float>) : reinterpret_cast<const void*>(&sample_kernel<13, 13, false, float>);
+        case 14: return grad ? reinterpret_cast<const void*>(&sample_kernel<14, 14, true, float>) : reinterpret_cast<const void*>(&sample_kernel<14, 14, false, float>);
+        case 15: return grad ? reinterpret_cast<const void*>(&sample_kernel<15, 15, true, float>) : reinterpret_cast<const void*>(&sample_kernel<15, 15, false, float>);
+        case 16: return grad ? reinterpret_cast<const void*>(&sample_kernel<16, 16, true, float>) : reinterpret_cast<const void*>(&sample_kernel<16, 16, false, float>);
+        case 17: return grad ? reinterpret_cast<const void*>(&sample_kernel<17, 17, true, float>) : reinterpret_cast<const void*>(&sample_kernel<17, 17, false, float>);
+        case 18: return grad ? reinterpret_cast<const void*>(&sample_kernel<18, 18, true, float>) : reinterpret_cast<const void*>(&sample_kernel<18, 18, false, float>);
+        case 19: return grad ? reinterpret_cast<const void*>(&sample_kernel<19, 19, true, float>) : reinterpret_cast<const void*>(&sample_kernel<19, 19, false, float>);
+        case 20: return grad ? reinterpret_cast<const void*>(&sample_kernel<20, 20, true, float>) : reinterpret_cast<const void*>(&sample_kernel<20, 20, false, float>);
         default: return nullptr;
     }
 }

@@ -133,14 +133,16 @@ __device__ __forceinline__ float d2f_bits(unsigned long long b) {
     return __uint_as_float((hi & 0x80000000u) | mag);
 }
 
-// FP32 -> FP64 bits, exact (FP32 subnormals flush to zero).
+// FP32 -> FP64 bits, exact for normal numbers (FP32 subnormals flush to
+// signed zero; infinity and NaN keep their class).
 __device__ __forceinline__ unsigned long long f2d_bits(float f) {
     const unsigned u = __float_as_uint(f);
-    const unsigned e = (u >> 23) & 0xffu;
-    if (e == 0u) return static_cast<unsigned long long>(u & 0x80000000u) << 32;
-    const unsigned hi = (u & 0x80000000u) | (e == 0xffu ? (0x7ffu << 20) | ((u >> 3) & 0xfffffu)
-                                                         : ((u & 0x7fffffffu) >> 3) + (896u << 20));
-    return (static_cast<unsigned long long>(hi) << 32) | (u << 29);
+    const unsigned sign = u & 0x80000000u, ex = u & 0x7f800000u;
+    unsigned hi = sign | (((u & 0x7fffffffu) >> 3) + (896u << 20));
+    unsigned lo = u << 29;
+    if (ex == 0u) { hi = sign; lo = 0u; }
+    if (ex == 0x7f800000u) hi = sign | 0x7ff00000u | ((u >> 3) & 0xfffffu);
+    return (static_cast<unsigned long long>(hi) << 32) | lo;
 }
 
 // Monotone map of FP64 bit patterns to unsigned keys (larger value, larger key).
@@ -198,9 +200,12 @@ struct RunMax {
 };
 
 // 2-D stencil: block = kRowsPerBlock x kColsPerBlock outputs of one scenario.
-// Staging: warp w copies tile rows w, w+8, ... (lanes along the row, no
-// index division), converting FP64 to FP32; then each thread slides a
-// (2R+1) x (2R+1) register window down kRowsPerThread rows of one column.
+// Staging: warp w copies tile rows w, w+8, ... (lanes along the row, the
+// column bounds fixed per lane), converting FP64 to FP32.  Compute: a thread
+// owns kRowsPerThread rows of one column; when all of them and the column are
+// interior (R points on every side) it slides a (2R+1)^2 register window down
+// the rows with the interior stencil in registers and no per-row tests; edge
+// threads take a plain loop with the stencil of each point's edge class.
 template <int R>
 __global__ void __launch_bounds__(256) smooth2d_kernel(const unsigned long long* __restrict__ val, int g1, int g2,
                                                        const float* __restrict__ w32,
@@ -219,25 +224,29 @@ __global__ void __launch_bounds__(256) smooth2d_kernel(const unsigned long long*
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     RunMax raw;
     raw.init();
+    bool col_in[CPL], col_own[CPL];
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+        const int cc = lane + 32 * k, gc = c0 - R + cc;
+        col_in[k] = cc < SC && gc >= 0 && gc < g2;
+        col_own[k] = cc >= R && cc < R + kColsPerBlock;
+    }
     for (int rr = warp; rr < SR; rr += 8) {
         const int gr = r0 - R + rr;
         const bool row_in = gr >= 0 && gr < g1;
         const bool row_own = rr >= R && rr < R + kRowsPerBlock;
-        const unsigned long long* rowp = V + static_cast<int64_t>(gr) * g2;
+        const unsigned long long* rowp = V + static_cast<int64_t>(gr) * g2 + (c0 - R + lane);
         unsigned long long bits[CPL];
 #pragma unroll
-        for (int k = 0; k < CPL; ++k) {
-            const int cc = lane + 32 * k, gc = c0 - R + cc;
-            bits[k] = (row_in && cc < SC && gc >= 0 && gc < g2) ? __ldg(rowp + gc) : 0ull;
-        }
+        for (int k = 0; k < CPL; ++k) bits[k] = (row_in && col_in[k]) ? __ldg(rowp + 32 * k) : 0ull;
 #pragma unroll
         for (int k = 0; k < CPL; ++k) {
-            const int cc = lane + 32 * k, gc = c0 - R + cc;
+            const int cc = lane + 32 * k;
             if (cc < SC) {
-                const bool in = row_in && gc >= 0 && gc < g2;
+                const bool in = row_in && col_in[k];
                 const float x = in ? d2f_bits(bits[k]) : 0.0f;
-                if (in && row_own && cc >= R && cc < R + kColsPerBlock)
-                    raw.add(x, bits[k], static_cast<long long>(gr) * g2 + gc);
+                if (in && row_own && col_own[k])
+                    raw.add(x, bits[k], static_cast<long long>(gr) * g2 + (c0 - R + cc));
                 tile[rr][cc] = x;
             }
         }
@@ -246,23 +255,24 @@ __global__ void __launch_bounds__(256) smooth2d_kernel(const unsigned long long*
     const int tx = threadIdx.x % kColsPerBlock;
     const int ty = threadIdx.x / kColsPerBlock;           // 0..1
     const int c = c0 + tx;
+    const int rb = ty * kRowsPerThread;                    // first tile row of this thread
+    const int rfirst = r0 + rb;                            // its first grid row
     float best = -INFINITY;
     long long best_i = -1;
-    if (c < g2) {
-        const int ncls = (R + 1) * (R + 1);
-        const int interior = R * (R + 1) + R;             // class with R points on both sides
-        const int ccls = cls(c, g2, R);
-        const bool cin = (ccls == interior);
+    const int ncls = (R + 1) * (R + 1);
+    const int interior = R * (R + 1) + R;                  // class with R points on both sides
+    const bool fast = c >= R && c <= g2 - 1 - R && rfirst >= R && rfirst + kRowsPerThread - 1 <= g1 - 1 - R;
+    if (fast) {
         float wi[T * T];                                   // interior stencil, in registers
 #pragma unroll
         for (int q = 0; q < T * T; ++q) wi[q] = __ldg(&w32[static_cast<int64_t>(interior * ncls + interior) * kMaxTaps + q]);
         float win[T][T];
-        const int rb = ty * kRowsPerThread;
 #pragma unroll
         for (int dx = 0; dx < T - 1; ++dx)
 #pragma unroll
             for (int dy = 0; dy < T; ++dy) win[dx + 1][dy] = tile[rb + dx][tx + dy];
-        unsigned long long* orow = out ? out + static_cast<int64_t>(s) * g1 * g2 + c : nullptr;
+        unsigned long long* op = out ? out + static_cast<int64_t>(s) * g1 * g2 + static_cast<int64_t>(rfirst) * g2 + c
+                                     : nullptr;
 #pragma unroll
         for (int k = 0; k < kRowsPerThread; ++k) {
 #pragma unroll
@@ -271,26 +281,30 @@ __global__ void __launch_bounds__(256) smooth2d_kernel(const unsigned long long*
                 for (int dy = 0; dy < T; ++dy) win[dx][dy] = win[dx + 1][dy];
 #pragma unroll
             for (int dy = 0; dy < T; ++dy) win[T - 1][dy] = tile[rb + k + T - 1][tx + dy];
-            const int r = r0 + rb + k;
-            if (r < g1) {
-                float acc = 0.0f;
-                const bool rin = (r >= R) && (r <= g1 - 1 - R);
-                if (cin && rin) {
+            float acc = 0.0f;
 #pragma unroll
-                    for (int dx = 0; dx < T; ++dx)
+            for (int dx = 0; dx < T; ++dx)
 #pragma unroll
-                        for (int dy = 0; dy < T; ++dy) acc = fmaf(wi[dx * T + dy], win[dx][dy], acc);
-                } else {
-                    const float* w = w32 + static_cast<int64_t>(cls(r, g1, R) * ncls + ccls) * kMaxTaps;
+                for (int dy = 0; dy < T; ++dy) acc = fmaf(wi[dx * T + dy], win[dx][dy], acc);
+            if (op) op[static_cast<int64_t>(k) * g2] = f2d_bits(acc);
+            // rows come in increasing index order: strict > keeps the lowest index
+            if (acc > best) { best = acc; best_i = k; }
+        }
+        if (best_i >= 0) best_i = static_cast<long long>(rfirst + best_i) * g2 + c;
+    } else if (c < g2) {
+        const int ccls = cls(c, g2, R);
+        for (int k = 0; k < kRowsPerThread; ++k) {
+            const int r = rfirst + k;
+            if (r >= g1) break;
+            const float* w = w32 + static_cast<int64_t>(cls(r, g1, R) * ncls + ccls) * kMaxTaps;
+            float acc = 0.0f;
 #pragma unroll
-                    for (int dx = 0; dx < T; ++dx)
+            for (int dx = 0; dx < T; ++dx)
 #pragma unroll
-                        for (int dy = 0; dy < T; ++dy) acc = fmaf(__ldg(&w[dx * T + dy]), win[dx][dy], acc);
-                }
-                if (orow) orow[static_cast<int64_t>(r) * g2] = f2d_bits(acc);
-                // rows of this thread come in increasing index order: strict > keeps the lowest
-                if (acc > best) { best = acc; best_i = static_cast<long long>(r) * g2 + c; }
-            }
+                for (int dy = 0; dy < T; ++dy) acc = fmaf(__ldg(&w[dx * T + dy]), tile[rb + k + dx][tx + dy], acc);
+            const long long idx = static_cast<long long>(r) * g2 + c;
+            if (out) out[static_cast<int64_t>(s) * g1 * g2 + idx] = f2d_bits(acc);
+            if (acc > best) { best = acc; best_i = idx; }
         }
     }
     unsigned long long best_k = best_i >= 0 ? order_key(f2d_bits(best)) : 0ull;
