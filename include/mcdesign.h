@@ -166,6 +166,32 @@ mcd_status mc_design_grad(mcd_ctx* ctx, const mcd_problem* prob, uint64_t seed,
                           uint64_t* hits, double* p, double* grad_lr, double* grad_sig,
                           double* grad_se, mcd_stream stream);
 
+/* Estimate p for the designs of one scenario without allocating memory.
+ * The paper has no counterpart: this is an entry point for callers that
+ * cannot allocate device memory at the point where they evaluate designs --
+ * code that hands all device memory to its own pool up front (a stray
+ * cudaMalloc there can fail or fragment the pool), loops that must not take
+ * the implicit synchronisation of cudaMalloc / cudaFree, processes whose
+ * allocator belongs to another runtime.  It needs no context and calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *   Scratch: the hit counters, stream keys and Cholesky factor live in one
+ *   static device array of the library (about 260 KB, held on every GPU that
+ *   loads the library until the process exits).  All calls share it and it
+ *   keeps the last call's contents (the counters are cleared by each call);
+ *   calls whose GPU work overlaps -- on different streams, or from several
+ *   host threads -- race on it and must be serialised by the caller.
+ *   Set-up: the first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   Limits: n_scen == 1, n_design <= 16384, every n_draws[j] equal,
+ *   draw_begin NULL or all 0; otherwise MCD_EINVAL, before any work.
+ *   Inputs and outputs as in mc_design_eval (the stream keys are copied from
+ *   the HOST array on `stream`).  A non-positive-definite Sigma gives p = se =
+ *   NaN and hits = 0 for every design, a NaN in mu_j or b_j the same for
+ *   design j; hits are bit-identical to mc_design_eval's otherwise. */
+mcd_status mc_design_eval_noalloc(int device, const mcd_problem* prob, uint64_t seed,
+                                  uint64_t* hits, double* p, double* se, mcd_stream stream);
+
 /* ---- smoothing and argmax (Sec. 2.3) ------------------------------------ */
 
 /* Local-polynomial smoothing of n_scen grids of g1 x g2 values (row-major,

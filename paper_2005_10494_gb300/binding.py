@@ -67,6 +67,7 @@ def load(path=LIB_PATH):
         "mc_design_grad": (i32, [vp, ctypes.POINTER(CProblem), u64, i32, vp, f64, vp, vp, vp, vp, vp, vp]),
         "mc_smooth_argmax": (i32, [vp, i32, i32, i32, vp, f64, i32, vp, vp, vp, vp, vp, vp]),
         "mcd_debug_normals": (i32, [vp, u64, u64, u64, u64, vp, vp, vp, vp]),
+        "mc_design_eval_noalloc": (i32, [ctypes.c_int, ctypes.POINTER(CProblem), u64, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -267,6 +268,20 @@ def mc_design_eval(ctx, prob, seed, stream=None):
     o = _outputs(prob.n_design, prob.vec_len, 0, False, prob.Sigma.device, False)
     ctx.check(ctx.lib.mc_design_eval(ctx.handle, ctypes.byref(prob.c), seed, _ptr(o["hits"]), _ptr(o["p"]),
                                      _ptr(o["se"]), _stream(stream)))
+    return _trim(o, prob.n_design, 0)
+
+
+def mc_design_eval_noalloc(prob, seed, device=0, stream=None, out=None):
+    """mc_design_eval for callers that cannot allocate device memory: one
+    scenario, equal draw counts, at most 16384 designs; the library's static
+    scratch array is shared by all calls (serialise overlapping calls).  Pass
+    preallocated `out` tensors (hits int64, p, se float64) to allocate nothing."""
+    lib = load()
+    o = out or _outputs(prob.n_design, prob.vec_len, 0, False, prob.Sigma.device, False)
+    rc = lib.mc_design_eval_noalloc(device, ctypes.byref(prob.c), seed, _ptr(o["hits"]), _ptr(o["p"]),
+                                    _ptr(o["se"]), _stream(stream))
+    if rc != MCD_OK:
+        raise MCDError(rc, "mc_design_eval_noalloc rejected the call")
     return _trim(o, prob.n_design, 0)
 
 
