@@ -23,7 +23,6 @@ constexpr int kMaxReach = 3;
 constexpr int kMaxTaps = (2 * kMaxReach + 1) * (2 * kMaxReach + 1);
 constexpr int kRowsPerBlock = 32;     // output rows of one block (2-D)
 constexpr int kColsPerBlock = 128;    // output columns of one block (2-D)
-constexpr int kRowsPerThread = 16;
 constexpr int kLine = 512;            // outputs of one block (1-D)
 
 __host__ __device__ inline int reach_of(double bw) {
@@ -126,10 +125,11 @@ __device__ __forceinline__ int cls(int i, int G, int R) {
 __device__ __forceinline__ float d2f_bits(unsigned long long b) {
     const unsigned hi = static_cast<unsigned>(b >> 32), lo = static_cast<unsigned>(b);
     const unsigned e = (hi >> 20) & 0x7ffu;
-    unsigned mag = __funnelshift_l(lo, hi, 3) - (896u << 23);
-    mag += (lo >> 28) & 1u;                                   // round half up (carry may reach the exponent)
-    if (e <= 896u) mag = 0u;
-    if (e >= 1151u) mag = (e == 0x7ffu && ((hi & 0xfffffu) | lo)) ? 0x7fc00000u : 0x7f800000u;
+    unsigned mag = __funnelshift_l(lo, hi, 3) - (896u << 23) + ((lo >> 28) & 1u);
+    if (e - 897u >= 254u) {                                   // outside the FP32 normal range
+        mag = e <= 896u ? 0u
+            : ((e == 0x7ffu && ((hi & 0xfffffu) | lo)) ? 0x7fc00000u : 0x7f800000u);
+    }
     return __uint_as_float((hi & 0x80000000u) | mag);
 }
 
@@ -201,11 +201,12 @@ struct RunMax {
 
 // 2-D stencil: block = kRowsPerBlock x kColsPerBlock outputs of one scenario.
 // Staging: warp w copies tile rows w, w+8, ... (lanes along the row, the
-// column bounds fixed per lane), converting FP64 to FP32.  Compute: a thread
-// owns kRowsPerThread rows of one column; when all of them and the column are
-// interior (R points on every side) it slides a (2R+1)^2 register window down
-// the rows with the interior stencil in registers and no per-row tests; edge
-// threads take a plain loop with the stencil of each point's edge class.
+// column bounds fixed per lane), converting FP64 to FP32.  Compute: thread
+// (tx, ty) owns the 4 x 4 outputs at rows 4 ty.., columns 4 tx..; when all of
+// them are interior (R points on every side) it streams the 4 + 2R input rows
+// of its window through registers with 16-byte shared loads and applies the
+// interior stencil (in registers); edge threads use each point's edge-class
+// stencil with scalar loads.
 template <int R>
 __global__ void __launch_bounds__(256) smooth2d_kernel(const unsigned long long* __restrict__ val, int g1, int g2,
                                                        const float* __restrict__ w32,
@@ -214,8 +215,11 @@ __global__ void __launch_bounds__(256) smooth2d_kernel(const unsigned long long*
                                                        unsigned long long* rpart_v, long long* rpart_i) {
     constexpr int T = 2 * R + 1;
     constexpr int SR = kRowsPerBlock + 2 * R, SC = kColsPerBlock + 2 * R;
+    constexpr int SCP = (SC + 3) / 4 * 4;                   // row stride: whole 16-byte vectors
     constexpr int CPL = (SC + 31) / 32;                     // row chunks per lane
-    __shared__ float tile[SR][SC];
+    constexpr int NIC = 4 + 2 * R;                          // input columns of a thread's window
+    constexpr int NV = (NIC + 3) / 4;                       // 16-byte loads per window row
+    __shared__ __align__(16) float tile[SR][SCP];
     __shared__ unsigned long long sv[8];
     __shared__ long long si[8];
     const int s = blockIdx.z;
@@ -242,7 +246,7 @@ __global__ void __launch_bounds__(256) smooth2d_kernel(const unsigned long long*
 #pragma unroll
         for (int k = 0; k < CPL; ++k) {
             const int cc = lane + 32 * k;
-            if (cc < SC) {
+            if (cc < SCP) {
                 const bool in = row_in && col_in[k];
                 const float x = in ? d2f_bits(bits[k]) : 0.0f;
                 if (in && row_own && col_own[k])
@@ -252,59 +256,81 @@ __global__ void __launch_bounds__(256) smooth2d_kernel(const unsigned long long*
         }
     }
     __syncthreads();
-    const int tx = threadIdx.x % kColsPerBlock;
-    const int ty = threadIdx.x / kColsPerBlock;           // 0..1
-    const int c = c0 + tx;
-    const int rb = ty * kRowsPerThread;                    // first tile row of this thread
-    const int rfirst = r0 + rb;                            // its first grid row
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int orow = r0 + 4 * ty, ocol = c0 + 4 * tx;       // first output of this thread
     float best = -INFINITY;
     long long best_i = -1;
     const int ncls = (R + 1) * (R + 1);
     const int interior = R * (R + 1) + R;                  // class with R points on both sides
-    const bool fast = c >= R && c <= g2 - 1 - R && rfirst >= R && rfirst + kRowsPerThread - 1 <= g1 - 1 - R;
+    unsigned long long* O = out ? out + static_cast<int64_t>(s) * g1 * g2 : nullptr;
+    const bool fast = ocol >= R && ocol + 3 <= g2 - 1 - R && orow >= R && orow + 3 <= g1 - 1 - R;
     if (fast) {
         float wi[T * T];                                   // interior stencil, in registers
 #pragma unroll
         for (int q = 0; q < T * T; ++q) wi[q] = __ldg(&w32[static_cast<int64_t>(interior * ncls + interior) * kMaxTaps + q]);
-        float win[T][T];
+        float acc[4][4];
 #pragma unroll
-        for (int dx = 0; dx < T - 1; ++dx)
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int dy = 0; dy < T; ++dy) win[dx + 1][dy] = tile[rb + dx][tx + dy];
-        unsigned long long* op = out ? out + static_cast<int64_t>(s) * g1 * g2 + static_cast<int64_t>(rfirst) * g2 + c
-                                     : nullptr;
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
 #pragma unroll
-        for (int k = 0; k < kRowsPerThread; ++k) {
+        for (int ir = 0; ir < 4 + 2 * R; ++ir) {
+            float in[4 * NV];
+            const float4* src = reinterpret_cast<const float4*>(&tile[4 * ty + ir][4 * tx]);
 #pragma unroll
-            for (int dx = 0; dx < T - 1; ++dx)
+            for (int v = 0; v < NV; ++v) {
+                const float4 q = src[v];
+                in[4 * v] = q.x; in[4 * v + 1] = q.y; in[4 * v + 2] = q.z; in[4 * v + 3] = q.w;
+            }
 #pragma unroll
-                for (int dy = 0; dy < T; ++dy) win[dx][dy] = win[dx + 1][dy];
+            for (int i = 0; i < 4; ++i) {
+                const int dx = ir - i;                      // window row of output row i
+                if (dx < 0 || dx >= T) continue;
 #pragma unroll
-            for (int dy = 0; dy < T; ++dy) win[T - 1][dy] = tile[rb + k + T - 1][tx + dy];
-            float acc = 0.0f;
+                for (int j = 0; j < 4; ++j)
 #pragma unroll
-            for (int dx = 0; dx < T; ++dx)
-#pragma unroll
-                for (int dy = 0; dy < T; ++dy) acc = fmaf(wi[dx * T + dy], win[dx][dy], acc);
-            if (op) op[static_cast<int64_t>(k) * g2] = f2d_bits(acc);
-            // rows come in increasing index order: strict > keeps the lowest index
-            if (acc > best) { best = acc; best_i = k; }
+                    for (int dy = 0; dy < T; ++dy) acc[i][j] = fmaf(wi[dx * T + dy], in[j + dy], acc[i][j]);
+            }
         }
-        if (best_i >= 0) best_i = static_cast<long long>(rfirst + best_i) * g2 + c;
-    } else if (c < g2) {
-        const int ccls = cls(c, g2, R);
-        for (int k = 0; k < kRowsPerThread; ++k) {
-            const int r = rfirst + k;
+        // 16-byte stores when the row starts stay 16-byte aligned
+        const bool vec = (g2 % 2) == 0 && (reinterpret_cast<uintptr_t>(O) & 15u) == 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const long long idx0 = static_cast<long long>(orow + i) * g2 + ocol;
+            if (O) {
+                const unsigned long long o0 = f2d_bits(acc[i][0]), o1 = f2d_bits(acc[i][1]);
+                const unsigned long long o2 = f2d_bits(acc[i][2]), o3 = f2d_bits(acc[i][3]);
+                if (vec) {
+                    ulonglong2* dst = reinterpret_cast<ulonglong2*>(O + idx0);
+                    dst[0] = make_ulonglong2(o0, o1);
+                    dst[1] = make_ulonglong2(o2, o3);
+                } else {
+                    O[idx0] = o0; O[idx0 + 1] = o1; O[idx0 + 2] = o2; O[idx0 + 3] = o3;
+                }
+            }
+            // outputs in increasing index order: strict > keeps the lowest index
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (acc[i][j] > best) { best = acc[i][j]; best_i = idx0 + j; }
+        }
+    } else {
+        for (int i = 0; i < 4; ++i) {
+            const int r = orow + i;
             if (r >= g1) break;
-            const float* w = w32 + static_cast<int64_t>(cls(r, g1, R) * ncls + ccls) * kMaxTaps;
-            float acc = 0.0f;
+            for (int j = 0; j < 4; ++j) {
+                const int c = ocol + j;
+                if (c >= g2) break;
+                const float* w = w32 + static_cast<int64_t>(cls(r, g1, R) * ncls + cls(c, g2, R)) * kMaxTaps;
+                float acc = 0.0f;
 #pragma unroll
-            for (int dx = 0; dx < T; ++dx)
+                for (int dx = 0; dx < T; ++dx)
 #pragma unroll
-                for (int dy = 0; dy < T; ++dy) acc = fmaf(__ldg(&w[dx * T + dy]), tile[rb + k + dx][tx + dy], acc);
-            const long long idx = static_cast<long long>(r) * g2 + c;
-            if (out) out[static_cast<int64_t>(s) * g1 * g2 + idx] = f2d_bits(acc);
-            if (acc > best) { best = acc; best_i = idx; }
+                    for (int dy = 0; dy < T; ++dy)
+                        acc = fmaf(__ldg(&w[dx * T + dy]), tile[4 * ty + i + dx][4 * tx + j + dy], acc);
+                const long long idx = static_cast<long long>(r) * g2 + c;
+                if (O) O[idx] = f2d_bits(acc);
+                if (acc > best) { best = acc; best_i = idx; }
+            }
         }
     }
     unsigned long long best_k = best_i >= 0 ? order_key(f2d_bits(best)) : 0ull;
