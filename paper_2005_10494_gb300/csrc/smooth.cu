@@ -263,8 +263,9 @@ __global__ void __launch_bounds__(256) smooth2d_kernel(const unsigned long long*
     const int ncls = (R + 1) * (R + 1);
     const int interior = R * (R + 1) + R;                  // class with R points on both sides
     unsigned long long* O = out ? out + static_cast<int64_t>(s) * g1 * g2 : nullptr;
-    const bool fast = ocol >= R && ocol + 3 <= g2 - 1 - R && orow >= R && orow + 3 <= g1 - 1 - R;
-    if (fast) {
+    // Phase A, no divergence: every thread applies the interior stencil to its
+    // whole 4 x 4 patch and keeps the outputs whose edge class is interior.
+    {
         float wi[T * T];                                   // interior stencil, in registers
 #pragma unroll
         for (int q = 0; q < T * T; ++q) wi[q] = __ldg(&w32[static_cast<int64_t>(interior * ncls + interior) * kMaxTaps + q]);
@@ -292,45 +293,79 @@ __global__ void __launch_bounds__(256) smooth2d_kernel(const unsigned long long*
                     for (int dy = 0; dy < T; ++dy) acc[i][j] = fmaf(wi[dx * T + dy], in[j + dy], acc[i][j]);
             }
         }
+        bool col_int[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) col_int[j] = ocol + j >= R && ocol + j <= g2 - 1 - R;
+        const bool all_cols = col_int[0] && col_int[3];
         // 16-byte stores when the row starts stay 16-byte aligned
         const bool vec = (g2 % 2) == 0 && (reinterpret_cast<uintptr_t>(O) & 15u) == 0;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
+            const bool row_int = orow + i >= R && orow + i <= g1 - 1 - R;
             const long long idx0 = static_cast<long long>(orow + i) * g2 + ocol;
-            if (O) {
-                const unsigned long long o0 = f2d_bits(acc[i][0]), o1 = f2d_bits(acc[i][1]);
-                const unsigned long long o2 = f2d_bits(acc[i][2]), o3 = f2d_bits(acc[i][3]);
-                if (vec) {
+            unsigned long long o[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) o[j] = f2d_bits(acc[i][j]);
+            if (O && row_int) {
+                if (vec && all_cols) {
                     ulonglong2* dst = reinterpret_cast<ulonglong2*>(O + idx0);
-                    dst[0] = make_ulonglong2(o0, o1);
-                    dst[1] = make_ulonglong2(o2, o3);
+                    dst[0] = make_ulonglong2(o[0], o[1]);
+                    dst[1] = make_ulonglong2(o[2], o[3]);
                 } else {
-                    O[idx0] = o0; O[idx0 + 1] = o1; O[idx0 + 2] = o2; O[idx0 + 3] = o3;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) if (col_int[j]) O[idx0 + j] = o[j];
                 }
             }
             // outputs in increasing index order: strict > keeps the lowest index
 #pragma unroll
             for (int j = 0; j < 4; ++j)
-                if (acc[i][j] > best) { best = acc[i][j]; best_i = idx0 + j; }
+                if (row_int && col_int[j] && acc[i][j] > best) { best = acc[i][j]; best_i = idx0 + j; }
         }
-    } else {
-        for (int i = 0; i < 4; ++i) {
-            const int r = orow + i;
-            if (r >= g1) break;
-            for (int j = 0; j < 4; ++j) {
-                const int c = ocol + j;
-                if (c >= g2) break;
-                const float* w = w32 + static_cast<int64_t>(cls(r, g1, R) * ncls + cls(c, g2, R)) * kMaxTaps;
-                float acc = 0.0f;
+    }
+    // Phase B: the block's edge outputs (fewer than R rows or columns to a
+    // grid edge), one per thread, with the stencil of their edge class.
+    // Edge columns (all 32 rows) first, then edge rows (the other columns).
+    {
+        int ecol[2 * R], erow[2 * R];
+        int nec = 0, ner = 0;
 #pragma unroll
-                for (int dx = 0; dx < T; ++dx)
+        for (int k = 0; k < R; ++k) {
+            if (c0 + k < R && c0 + k < g2) ecol[nec++] = c0 + k;                 // left edge
+        }
 #pragma unroll
-                    for (int dy = 0; dy < T; ++dy)
-                        acc = fmaf(__ldg(&w[dx * T + dy]), tile[4 * ty + i + dx][4 * tx + j + dy], acc);
-                const long long idx = static_cast<long long>(r) * g2 + c;
-                if (O) O[idx] = f2d_bits(acc);
-                if (acc > best) { best = acc; best_i = idx; }
+        for (int k = 0; k < R; ++k) {
+            const int c = g2 - R + k;
+            if (c >= R && c >= c0 && c < c0 + kColsPerBlock) ecol[nec++] = c;     // right edge
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            if (r0 + k < R && r0 + k < g1) erow[ner++] = r0 + k;                 // top edge
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int r = g1 - R + k;
+            if (r >= R && r >= r0 && r < r0 + kRowsPerBlock) erow[ner++] = r;     // bottom edge
+        }
+        const int rows_here = min(kRowsPerBlock, g1 - r0);
+        const int n1 = nec * rows_here, n2 = ner * kColsPerBlock;
+        for (int t = threadIdx.x; t < n1 + n2; t += blockDim.x) {
+            int r, c;
+            if (t < n1) { c = ecol[t / rows_here]; r = r0 + t % rows_here; }
+            else {
+                r = erow[(t - n1) / kColsPerBlock];
+                c = c0 + (t - n1) % kColsPerBlock;
+                if (c >= g2 || c < R || c > g2 - 1 - R) continue;                // edge columns done above
             }
+            const float* w = w32 + static_cast<int64_t>(cls(r, g1, R) * ncls + cls(c, g2, R)) * kMaxTaps;
+            float acc = 0.0f;
+#pragma unroll
+            for (int dx = 0; dx < T; ++dx)
+#pragma unroll
+                for (int dy = 0; dy < T; ++dy)
+                    acc = fmaf(__ldg(&w[dx * T + dy]), tile[r - r0 + dx][c - c0 + dy], acc);
+            const long long idx = static_cast<long long>(r) * g2 + c;
+            if (O) O[idx] = f2d_bits(acc);
+            if (acc > best || (acc == best && idx < best_i)) { best = acc; best_i = idx; }
         }
     }
     unsigned long long best_k = best_i >= 0 ? order_key(f2d_bits(best)) : 0ull;
