@@ -295,15 +295,17 @@ def mc_design_grad(ctx, prob, seed, k=0, jac=None, h=0.0, stream=None):
     return _trim(o, prob.n_design, n)
 
 
-def mc_smooth_argmax(ctx, values, n_scen, g1, g2, bandwidth=3.0, degree=2, stream=None, smoothed=True):
-    """Smooth n_scen grids of g1 x g2 values (FP64 CUDA tensor) and take argmaxes."""
+def mc_smooth_argmax(ctx, values, n_scen, g1, g2, bandwidth=3.0, degree=2, stream=None, smoothed=True,
+                     raw=False):
+    """Smooth n_scen grids of g1 x g2 values (FP64 CUDA tensor) and take
+    argmaxes; raw=True also returns the argmax of the unsmoothed values."""
     torch = _torch()
     dev = values.device
     sm = torch.empty(n_scen * g1 * g2, dtype=torch.float64, device=dev) if smoothed else None
     idx = torch.empty(n_scen, dtype=torch.int64, device=dev)
     val = torch.empty(n_scen, dtype=torch.float64, device=dev)
-    ridx = torch.empty(n_scen, dtype=torch.int64, device=dev)
-    rval = torch.empty(n_scen, dtype=torch.float64, device=dev)
+    ridx = torch.empty(n_scen, dtype=torch.int64, device=dev) if raw else None
+    rval = torch.empty(n_scen, dtype=torch.float64, device=dev) if raw else None
     ctx.check(ctx.lib.mc_smooth_argmax(ctx.handle, n_scen, g1, g2, _ptr(values), float(bandwidth), degree,
                                        _ptr(sm), _ptr(idx), _ptr(val), _ptr(ridx), _ptr(rval), _stream(stream)))
     return {"smoothed": sm, "argmax_idx": idx, "argmax_val": val, "raw_idx": ridx, "raw_val": rval}

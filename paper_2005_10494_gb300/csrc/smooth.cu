@@ -117,15 +117,15 @@ __device__ __forceinline__ int cls(int i, int G, int R) {
 // edges: values are converted between FP64 and FP32 and ordered for the
 // argmax with integer operations on their bit patterns.
 
-// FP64 -> FP32 with rounding of the dropped bits half-up (error at most half
-// an FP32 ulp); magnitudes below the FP32 normal range become 0, above it
-// infinity, NaN stays NaN.  The mantissa and exponent move together with one
-// funnel shift: (hi:lo) << 3 puts the low 8 exponent bits and the top 23
-// mantissa bits in place, and subtracting (1023 - 127) << 23 rebiases.
+// FP64 -> FP32, truncating the dropped mantissa bits (error below one FP32
+// ulp); magnitudes below the FP32 normal range become 0, above it infinity,
+// NaN stays NaN.  The mantissa and exponent move together with one funnel
+// shift: (hi:lo) << 3 puts the low 8 exponent bits and the top 23 mantissa
+// bits in place, and subtracting (1023 - 127) << 23 rebiases.
 __device__ __forceinline__ float d2f_bits(unsigned long long b) {
     const unsigned hi = static_cast<unsigned>(b >> 32), lo = static_cast<unsigned>(b);
     const unsigned e = (hi >> 20) & 0x7ffu;
-    unsigned mag = __funnelshift_l(lo, hi, 3) - (896u << 23) + ((lo >> 28) & 1u);
+    unsigned mag = __funnelshift_l(lo, hi, 3) - (896u << 23);
     if (e - 897u >= 254u) {                                   // outside the FP32 normal range
         mag = e <= 896u ? 0u
             : ((e == 0x7ffu && ((hi & 0xfffffu) | lo)) ? 0x7fc00000u : 0x7f800000u);
@@ -137,12 +137,14 @@ __device__ __forceinline__ float d2f_bits(unsigned long long b) {
 // signed zero; infinity and NaN keep their class).
 __device__ __forceinline__ unsigned long long f2d_bits(float f) {
     const unsigned u = __float_as_uint(f);
-    const unsigned sign = u & 0x80000000u, ex = u & 0x7f800000u;
-    unsigned hi = sign | (((u & 0x7fffffffu) >> 3) + (896u << 20));
-    unsigned lo = u << 29;
-    if (ex == 0u) { hi = sign; lo = 0u; }
-    if (ex == 0x7f800000u) hi = sign | 0x7ff00000u | ((u >> 3) & 0xfffffu);
-    return (static_cast<unsigned long long>(hi) << 32) | lo;
+    const unsigned ex = u & 0x7f800000u, sign = u & 0x80000000u;
+    if (ex - 0x00800000u < 0x7f000000u) {                     // normal
+        const unsigned hi = sign | (((u & 0x7fffffffu) >> 3) + (896u << 20));
+        return (static_cast<unsigned long long>(hi) << 32) | (u << 29);
+    }
+    if (ex == 0u) return static_cast<unsigned long long>(sign) << 32;
+    const unsigned hi = sign | 0x7ff00000u | ((u >> 3) & 0xfffffu);
+    return (static_cast<unsigned long long>(hi) << 32) | (u << 29);
 }
 
 // Monotone map of FP64 bit patterns to unsigned keys (larger value, larger key).
@@ -207,7 +209,7 @@ struct RunMax {
 // of its window through registers with 16-byte shared loads and applies the
 // interior stencil (in registers); edge threads use each point's edge-class
 // stencil with scalar loads.
-template <int R>
+template <int R, bool RAW>
 __global__ void __launch_bounds__(256) smooth2d_kernel(const unsigned long long* __restrict__ val, int g1, int g2,
                                                        const float* __restrict__ w32,
                                                        unsigned long long* __restrict__ out,
@@ -222,6 +224,8 @@ __global__ void __launch_bounds__(256) smooth2d_kernel(const unsigned long long*
     __shared__ __align__(16) float tile[SR][SCP];
     __shared__ unsigned long long sv[8];
     __shared__ long long si[8];
+    __shared__ float sm_max[8];
+    __shared__ long long sm_idx;
     const int s = blockIdx.z;
     const int r0 = blockIdx.y * kRowsPerBlock, c0 = blockIdx.x * kColsPerBlock;
     const unsigned long long* V = val + static_cast<int64_t>(s) * g1 * g2;
@@ -249,7 +253,7 @@ __global__ void __launch_bounds__(256) smooth2d_kernel(const unsigned long long*
             if (cc < SCP) {
                 const bool in = row_in && col_in[k];
                 const float x = in ? d2f_bits(bits[k]) : 0.0f;
-                if (in && row_own && col_own[k])
+                if (RAW && in && row_own && col_own[k])
                     raw.add(x, bits[k], static_cast<long long>(gr) * g2 + (c0 - R + cc));
                 tile[rr][cc] = x;
             }
@@ -265,6 +269,7 @@ __global__ void __launch_bounds__(256) smooth2d_kernel(const unsigned long long*
     unsigned long long* O = out ? out + static_cast<int64_t>(s) * g1 * g2 : nullptr;
     // Phase A, no divergence: every thread applies the interior stencil to its
     // whole 4 x 4 patch and keeps the outputs whose edge class is interior.
+    float keep[4][4];
     {
         float wi[T * T];                                   // interior stencil, in registers
 #pragma unroll
@@ -316,15 +321,20 @@ __global__ void __launch_bounds__(256) smooth2d_kernel(const unsigned long long*
                     for (int j = 0; j < 4; ++j) if (col_int[j]) O[idx0 + j] = o[j];
                 }
             }
-            // outputs in increasing index order: strict > keeps the lowest index
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (row_int && col_int[j] && acc[i][j] > best) { best = acc[i][j]; best_i = idx0 + j; }
+            for (int j = 0; j < 4; ++j) best = fmaxf(best, (row_int && col_int[j]) ? acc[i][j] : -INFINITY);
         }
+        // keep the patch for the index search of the winning threads
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) keep[i][j] = acc[i][j];
     }
     // Phase B: the block's edge outputs (fewer than R rows or columns to a
     // grid edge), one per thread, with the stencil of their edge class.
     // Edge columns (all 32 rows) first, then edge rows (the other columns).
+    float eb_v = -INFINITY;
+    long long eb_i = -1;
     {
         int ecol[2 * R], erow[2 * R];
         int nec = 0, ner = 0;
@@ -365,19 +375,52 @@ __global__ void __launch_bounds__(256) smooth2d_kernel(const unsigned long long*
                     acc = fmaf(__ldg(&w[dx * T + dy]), tile[r - r0 + dx][c - c0 + dy], acc);
             const long long idx = static_cast<long long>(r) * g2 + c;
             if (O) O[idx] = f2d_bits(acc);
-            if (acc > best || (acc == best && idx < best_i)) { best = acc; best_i = idx; }
+            if (acc > eb_v || (acc == eb_v && idx < eb_i)) { eb_v = acc; eb_i = idx; }
         }
     }
-    unsigned long long best_k = best_i >= 0 ? order_key(f2d_bits(best)) : 0ull;
+    best = fmaxf(best, eb_v);
+    // Argmax: the block's largest value first (max reductions only), then the
+    // lowest index holding it, searched by the few threads that hold it.
+    {
+        float m = best;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0) sm_max[threadIdx.x >> 5] = m;
+        if (threadIdx.x == 0) sm_idx = -1;
+        __syncthreads();
+        float bm = sm_max[0];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) bm = fmaxf(bm, sm_max[w]);
+        if (best == bm && bm > -INFINITY) {
+            long long cand = (eb_v == bm) ? eb_i : -1;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const bool row_int = orow + i >= R && orow + i <= g1 - 1 - R;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const bool v = row_int && ocol + j >= R && ocol + j <= g2 - 1 - R && keep[i][j] == bm;
+                    const long long idx = static_cast<long long>(orow + i) * g2 + ocol + j;
+                    if (v && (cand < 0 || idx < cand)) cand = idx;
+                }
+            }
+            if (cand >= 0) atomicMin(reinterpret_cast<unsigned long long*>(&sm_idx), static_cast<unsigned long long>(cand));
+        }
+        __syncthreads();
+        best_i = sm_idx;
+        best = bm;
+    }
     const int nb = gridDim.x * gridDim.y;
     const int b = blockIdx.y * gridDim.x + blockIdx.x;
-    block_amax(best_k, best_i, sv, si);
-    if (threadIdx.x == 0) { part_v[static_cast<int64_t>(s) * nb + b] = best_k; part_i[static_cast<int64_t>(s) * nb + b] = best_i; }
-    __syncthreads();
-    unsigned long long raw_k = raw.key;
-    long long raw_i = raw.idx;
-    block_amax(raw_k, raw_i, sv, si);
-    if (threadIdx.x == 0) { rpart_v[static_cast<int64_t>(s) * nb + b] = raw_k; rpart_i[static_cast<int64_t>(s) * nb + b] = raw_i; }
+    if (threadIdx.x == 0) {
+        part_v[static_cast<int64_t>(s) * nb + b] = best_i >= 0 ? order_key(f2d_bits(best)) : 0ull;
+        part_i[static_cast<int64_t>(s) * nb + b] = best_i;
+    }
+    if constexpr (RAW) {
+        unsigned long long raw_k = raw.key;
+        long long raw_i = raw.idx;
+        block_amax(raw_k, raw_i, sv, si);
+        if (threadIdx.x == 0) { rpart_v[static_cast<int64_t>(s) * nb + b] = raw_k; rpart_i[static_cast<int64_t>(s) * nb + b] = raw_i; }
+    }
 }
 
 // 1-D stencil along a line of n points.
@@ -444,6 +487,7 @@ __global__ void argmax_kernel(int nb, const unsigned long long* part_v, const lo
         if (idx) idx[s] = bi;
         if (v) v[s] = bi >= 0 ? __longlong_as_double(static_cast<long long>(key_bits(bv))) : NAN;
     }
+    if (!ridx && !rv) return;
     __syncthreads();
     bv = 0;
     bi = -1;
@@ -500,9 +544,16 @@ cudaError_t smooth_argmax(int n_scen, int g1, int g2, const double* value, doubl
     unsigned long long* ob = reinterpret_cast<unsigned long long*>(smoothed);
     if (two_d) {
         dim3 grid((g2 + kColsPerBlock - 1) / kColsPerBlock, (g1 + kRowsPerBlock - 1) / kRowsPerBlock, n_scen);
-        if (R == 1) smooth2d_kernel<1><<<grid, 256, 0, stream>>>(vb, g1, g2, wbuf32, ob, pv, pi, rpv, rpi);
-        else if (R == 2) smooth2d_kernel<2><<<grid, 256, 0, stream>>>(vb, g1, g2, wbuf32, ob, pv, pi, rpv, rpi);
-        else smooth2d_kernel<3><<<grid, 256, 0, stream>>>(vb, g1, g2, wbuf32, ob, pv, pi, rpv, rpi);
+        const bool raw = raw_idx || raw_val;
+        if (raw) {
+            if (R == 1) smooth2d_kernel<1, true><<<grid, 256, 0, stream>>>(vb, g1, g2, wbuf32, ob, pv, pi, rpv, rpi);
+            else if (R == 2) smooth2d_kernel<2, true><<<grid, 256, 0, stream>>>(vb, g1, g2, wbuf32, ob, pv, pi, rpv, rpi);
+            else smooth2d_kernel<3, true><<<grid, 256, 0, stream>>>(vb, g1, g2, wbuf32, ob, pv, pi, rpv, rpi);
+        } else {
+            if (R == 1) smooth2d_kernel<1, false><<<grid, 256, 0, stream>>>(vb, g1, g2, wbuf32, ob, pv, pi, rpv, rpi);
+            else if (R == 2) smooth2d_kernel<2, false><<<grid, 256, 0, stream>>>(vb, g1, g2, wbuf32, ob, pv, pi, rpv, rpi);
+            else smooth2d_kernel<3, false><<<grid, 256, 0, stream>>>(vb, g1, g2, wbuf32, ob, pv, pi, rpv, rpi);
+        }
     } else {
         dim3 grid(nb, n_scen);
         const int n = g1 * g2;

@@ -278,8 +278,12 @@ def test_smoothing_matches_oracle(ctx, shape, bw, deg):
     vals = np.stack([0.7 - 0.0004 * (i - g1 / 3) ** 2 - 0.0002 * (j - g2 / 2) ** 2 + rng.normal(0, 0.01, (g1, g2))
                      for _ in range(S)])
     v = torch.as_tensor(vals.ravel(), dtype=torch.float64, device="cuda")
-    r = pkg.mc_smooth_argmax(ctx, v, S, g1, g2, bandwidth=bw, degree=deg)
+    r = pkg.mc_smooth_argmax(ctx, v, S, g1, g2, bandwidth=bw, degree=deg, raw=True)
     ctx.sync_status()
+    r2 = pkg.mc_smooth_argmax(ctx, v, S, g1, g2, bandwidth=bw, degree=deg)     # without the raw argmax
+    ctx.sync_status()
+    np.testing.assert_array_equal(r2["argmax_idx"].cpu().numpy(), r["argmax_idx"].cpu().numpy())
+    np.testing.assert_array_equal(r2["smoothed"].cpu().numpy(), r["smoothed"].cpu().numpy())
     sm_ref, idx_ref, val_ref, ridx_ref, rval_ref = smooth.smooth_argmax(vals, g1, g2, bw, deg)
     sm = r["smoothed"].cpu().numpy().reshape(S, g1, g2)
     np.testing.assert_allclose(sm, sm_ref, rtol=0, atol=2e-6)
