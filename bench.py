@@ -197,8 +197,9 @@ def run_reference(args, rank):
 
 
 # ------------------------------------------------------------ our arm
-def traffic_record():
-    """DRAM bytes per sampling launch from the committed ncu summary, or None
+def traffic_record(tiles):
+    """DRAM bytes of one sampling launch of `tiles` tiles, from the committed
+    ncu capture of a small case (traffic grows with the tile count), or None
     when the kernel sources changed since that capture."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
@@ -215,9 +216,10 @@ def traffic_record():
     if rec.get("src_sha256") != h.hexdigest():
         return None
     try:
-        return float(rec["dram_bytes_per_launch_full"])
-    except (KeyError, ValueError):
+        per_tile = (float(rec["dram_bytes_read_small"]) + float(rec["dram_bytes_write_small"])) / float(rec["tiles_small"])
+    except (KeyError, ValueError, ZeroDivisionError):
         return None
+    return per_tile * tiles
 
 
 def kernel_rate(pkg, ctx, prob, grad, reps=2, h=0.01):
@@ -311,7 +313,7 @@ def run_ours(args, rank, world):
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_ops = sm_count * LANES * SM_MAX_MHZ * 1e6
     achieved = ops * draws / (kernel_ms / 1e3)
-    traffic = traffic_record()
+    traffic = traffic_record(plan.tiles())
     fp32 = fp32_flops_per_draw(3, True) * draws / (kernel_ms / 1e3)
     fp32_peak = sm_count * LANES * 2 * SM_MAX_MHZ * 1e6
 
