@@ -10,7 +10,6 @@
 // linear stencil for each pair of edge classes (distance to the low and high
 // edge, capped at the reach R), so the FP64 solve runs once per class pair
 // and the application over the grid is a stencil, HBM-bound, in FP32.
-#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -202,271 +201,225 @@ struct RunMax {
     }
 };
 
-// Asynchronous 8-byte global -> shared copy; src_bytes = 0 fills zeros
-// without reading (the source address must still be a valid pointer).
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool valid) {
-    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-    const int n = valid ? 8 : 0;
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(n) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-
-template <int R>
-struct Smooth2dShape {
-    static constexpr int T = 2 * R + 1;
-    static constexpr int SR = kRowsPerBlock + 2 * R, SC = kColsPerBlock + 2 * R;
-    static constexpr int SCP = (SC + 3) / 4 * 4;            // FP32 row stride: whole 16-byte vectors
-    static constexpr size_t kStage = static_cast<size_t>(SR) * SC * sizeof(double);
-    static constexpr size_t kSmem = 2 * kStage + static_cast<size_t>(SR) * SCP * sizeof(float);
-};
-
-// 2-D stencil, persistent over output tiles of kRowsPerBlock x kColsPerBlock
-// points (tile t: scenario t / (tiles per grid), then row band, then column
-// band).  While tile t is smoothed from one shared FP64 buffer, tile t + grid
-// is copied into the other by cp.async (zero-filled outside the grid), so the
-// loads of the next tile overlap the work on this one.  Per tile: warp w
-// converts tile rows w, w+8, ... from FP64 to an FP32 tile; thread (tx, ty)
-// owns the 4 x 4 outputs at rows 4 ty.., columns 4 tx.. and applies the
-// interior stencil to all of them (no divergence), keeping the interior
-// ones; the few edge outputs are then spread one per thread with their
-// edge-class stencils.
+// 2-D stencil: block = kRowsPerBlock x kColsPerBlock outputs of one scenario.
+// Staging: warp w copies tile rows w, w+8, ... (lanes along the row, the
+// column bounds fixed per lane), converting FP64 to FP32.  Compute: thread
+// (tx, ty) owns the 4 x 4 outputs at rows 4 ty.., columns 4 tx..; when all of
+// them are interior (R points on every side) it streams the 4 + 2R input rows
+// of its window through registers with 16-byte shared loads and applies the
+// interior stencil (in registers); edge threads use each point's edge-class
+// stencil with scalar loads.
 template <int R, bool RAW>
-__global__ void __launch_bounds__(256) smooth2d_kernel(const unsigned long long* __restrict__ val, int n_scen,
-                                                       int g1, int g2, const float* __restrict__ w32,
+__global__ void __launch_bounds__(256) smooth2d_kernel(const unsigned long long* __restrict__ val, int g1, int g2,
+                                                       const float* __restrict__ w32,
                                                        unsigned long long* __restrict__ out,
                                                        unsigned long long* part_v, long long* part_i,
                                                        unsigned long long* rpart_v, long long* rpart_i) {
-    using SH = Smooth2dShape<R>;
-    constexpr int T = SH::T, SR = SH::SR, SC = SH::SC, SCP = SH::SCP;
+    constexpr int T = 2 * R + 1;
+    constexpr int SR = kRowsPerBlock + 2 * R, SC = kColsPerBlock + 2 * R;
+    constexpr int SCP = (SC + 3) / 4 * 4;                   // row stride: whole 16-byte vectors
     constexpr int CPL = (SC + 31) / 32;                     // row chunks per lane
     constexpr int NIC = 4 + 2 * R;                          // input columns of a thread's window
     constexpr int NV = (NIC + 3) / 4;                       // 16-byte loads per window row
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    double (*stage)[SR][SC] = reinterpret_cast<double (*)[SR][SC]>(smem_raw);
-    float (*tile)[SCP] = reinterpret_cast<float (*)[SCP]>(smem_raw + 2 * SH::kStage);
+    __shared__ __align__(16) float tile[SR][SCP];
     __shared__ unsigned long long sv[8];
     __shared__ long long si[8];
     __shared__ float sm_max[8];
     __shared__ long long sm_idx;
-    const int nbx = (g2 + kColsPerBlock - 1) / kColsPerBlock, nby = (g1 + kRowsPerBlock - 1) / kRowsPerBlock;
-    const int nb = nbx * nby;
-    const long long total = static_cast<long long>(n_scen) * nb;
+    const int s = blockIdx.z;
+    const int r0 = blockIdx.y * kRowsPerBlock, c0 = blockIdx.x * kColsPerBlock;
+    const unsigned long long* V = val + static_cast<int64_t>(s) * g1 * g2;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-    // copy tile t into stage buffer `buf`
-    auto prefetch = [&](long long t, int buf) {
-        const int s = static_cast<int>(t / nb), rem = static_cast<int>(t % nb);
-        const int r0 = (rem / nbx) * kRowsPerBlock, c0 = (rem % nbx) * kColsPerBlock;
-        const unsigned long long* V = val + static_cast<int64_t>(s) * g1 * g2;
-        for (int rr = warp; rr < SR; rr += 8) {
-            const int gr = r0 - R + rr;
-            const bool row_in = gr >= 0 && gr < g1;
+    RunMax raw;
+    raw.init();
+    bool col_in[CPL], col_own[CPL];
 #pragma unroll
-            for (int k = 0; k < CPL; ++k) {
-                const int cc = lane + 32 * k, gc = c0 - R + cc;
-                if (cc < SC) {
-                    const bool in = row_in && gc >= 0 && gc < g2;
-                    cp_async8(&stage[buf][rr][cc], in ? V + static_cast<int64_t>(gr) * g2 + gc : val, in);
-                }
+    for (int k = 0; k < CPL; ++k) {
+        const int cc = lane + 32 * k, gc = c0 - R + cc;
+        col_in[k] = cc < SC && gc >= 0 && gc < g2;
+        col_own[k] = cc >= R && cc < R + kColsPerBlock;
+    }
+    for (int rr = warp; rr < SR; rr += 8) {
+        const int gr = r0 - R + rr;
+        const bool row_in = gr >= 0 && gr < g1;
+        const bool row_own = rr >= R && rr < R + kRowsPerBlock;
+        const unsigned long long* rowp = V + static_cast<int64_t>(gr) * g2 + (c0 - R + lane);
+        unsigned long long bits[CPL];
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) bits[k] = (row_in && col_in[k]) ? __ldg(rowp + 32 * k) : 0ull;
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) {
+            const int cc = lane + 32 * k;
+            if (cc < SCP) {
+                const bool in = row_in && col_in[k];
+                const float x = in ? d2f_bits(bits[k]) : 0.0f;
+                if (RAW && in && row_own && col_own[k])
+                    raw.add(x, bits[k], static_cast<long long>(gr) * g2 + (c0 - R + cc));
+                tile[rr][cc] = x;
             }
         }
-    };
-
-    long long t = blockIdx.x;
-    int buf = 0;
-    if (t < total) prefetch(t, 0);
-    cp_async_commit();
-    for (; t < total; t += gridDim.x, buf ^= 1) {
-        if (t + gridDim.x < total) prefetch(t + gridDim.x, buf ^ 1);
-        cp_async_commit();
-        cp_async_wait_prev();                               // tile t has landed
-        __syncthreads();
-        const int s = static_cast<int>(t / nb), rem = static_cast<int>(t % nb);
-        const int r0 = (rem / nbx) * kRowsPerBlock, c0 = (rem % nbx) * kColsPerBlock;
-        const int b = rem;
-        RunMax raw;
-        raw.init();
-        for (int rr = warp; rr < SR; rr += 8) {
-            const int gr = r0 - R + rr;
-            const bool row_in = gr >= 0 && gr < g1;
-            const bool row_own = rr >= R && rr < R + kRowsPerBlock;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int orow = r0 + 4 * ty, ocol = c0 + 4 * tx;       // first output of this thread
+    float best = -INFINITY;
+    long long best_i = -1;
+    const int ncls = (R + 1) * (R + 1);
+    const int interior = R * (R + 1) + R;                  // class with R points on both sides
+    unsigned long long* O = out ? out + static_cast<int64_t>(s) * g1 * g2 : nullptr;
+    // Phase A, no divergence: every thread applies the interior stencil to its
+    // whole 4 x 4 patch and keeps the outputs whose edge class is interior.
+    float keep[4][4];
+    {
+        float wi[T * T];                                   // interior stencil, in registers
 #pragma unroll
-            for (int k = 0; k < CPL; ++k) {
-                const int cc = lane + 32 * k, gc = c0 - R + cc;
-                if (cc < SCP) {
-                    float x = 0.0f;
-                    if (cc < SC) {
-                        const unsigned long long bits = __double_as_longlong(stage[buf][rr][cc]);
-                        x = d2f_bits(bits);
-                        if (RAW && row_in && row_own && gc >= 0 && gc < g2 && cc >= R && cc < R + kColsPerBlock)
-                            raw.add(x, bits, static_cast<long long>(gr) * g2 + gc);
-                    }
-                    tile[rr][cc] = x;
-                }
+        for (int q = 0; q < T * T; ++q) wi[q] = __ldg(&w32[static_cast<int64_t>(interior * ncls + interior) * kMaxTaps + q]);
+        float acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+#pragma unroll
+        for (int ir = 0; ir < 4 + 2 * R; ++ir) {
+            float in[4 * NV];
+            const float4* src = reinterpret_cast<const float4*>(&tile[4 * ty + ir][4 * tx]);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const float4 q = src[v];
+                in[4 * v] = q.x; in[4 * v + 1] = q.y; in[4 * v + 2] = q.z; in[4 * v + 3] = q.w;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int dx = ir - i;                      // window row of output row i
+                if (dx < 0 || dx >= T) continue;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int dy = 0; dy < T; ++dy) acc[i][j] = fmaf(wi[dx * T + dy], in[j + dy], acc[i][j]);
             }
         }
-        __syncthreads();
-        const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-        const int orow = r0 + 4 * ty, ocol = c0 + 4 * tx;       // first output of this thread
-        float best = -INFINITY;
-        long long best_i = -1;
-        const int ncls = (R + 1) * (R + 1);
-        const int interior = R * (R + 1) + R;                  // class with R points on both sides
-        unsigned long long* O = out ? out + static_cast<int64_t>(s) * g1 * g2 : nullptr;
-        // Phase A, no divergence: every thread applies the interior stencil to its
-        // whole 4 x 4 patch and keeps the outputs whose edge class is interior.
-        float keep[4][4];
-        {
-            float wi[T * T];                                   // interior stencil, in registers
-    #pragma unroll
-            for (int q = 0; q < T * T; ++q) wi[q] = __ldg(&w32[static_cast<int64_t>(interior * ncls + interior) * kMaxTaps + q]);
-            float acc[4][4];
-    #pragma unroll
-            for (int i = 0; i < 4; ++i)
-    #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
-    #pragma unroll
-            for (int ir = 0; ir < 4 + 2 * R; ++ir) {
-                float in[4 * NV];
-                const float4* src = reinterpret_cast<const float4*>(&tile[4 * ty + ir][4 * tx]);
-    #pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    const float4 q = src[v];
-                    in[4 * v] = q.x; in[4 * v + 1] = q.y; in[4 * v + 2] = q.z; in[4 * v + 3] = q.w;
-                }
-    #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int dx = ir - i;                      // window row of output row i
-                    if (dx < 0 || dx >= T) continue;
-    #pragma unroll
-                    for (int j = 0; j < 4; ++j)
-    #pragma unroll
-                        for (int dy = 0; dy < T; ++dy) acc[i][j] = fmaf(wi[dx * T + dy], in[j + dy], acc[i][j]);
+        bool col_int[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) col_int[j] = ocol + j >= R && ocol + j <= g2 - 1 - R;
+        const bool all_cols = col_int[0] && col_int[3];
+        // 16-byte stores when the row starts stay 16-byte aligned
+        const bool vec = (g2 % 2) == 0 && (reinterpret_cast<uintptr_t>(O) & 15u) == 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const bool row_int = orow + i >= R && orow + i <= g1 - 1 - R;
+            const long long idx0 = static_cast<long long>(orow + i) * g2 + ocol;
+            unsigned long long o[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) o[j] = f2d_bits(acc[i][j]);
+            if (O && row_int) {
+                if (vec && all_cols) {
+                    ulonglong2* dst = reinterpret_cast<ulonglong2*>(O + idx0);
+                    dst[0] = make_ulonglong2(o[0], o[1]);
+                    dst[1] = make_ulonglong2(o[2], o[3]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) if (col_int[j]) O[idx0 + j] = o[j];
                 }
             }
-            bool col_int[4];
-    #pragma unroll
-            for (int j = 0; j < 4; ++j) col_int[j] = ocol + j >= R && ocol + j <= g2 - 1 - R;
-            const bool all_cols = col_int[0] && col_int[3];
-            // 16-byte stores when the row starts stay 16-byte aligned
-            const bool vec = (g2 % 2) == 0 && (reinterpret_cast<uintptr_t>(O) & 15u) == 0;
-    #pragma unroll
+#pragma unroll
+            for (int j = 0; j < 4; ++j) best = fmaxf(best, (row_int && col_int[j]) ? acc[i][j] : -INFINITY);
+        }
+        // keep the patch for the index search of the winning threads
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) keep[i][j] = acc[i][j];
+    }
+    // Phase B: the block's edge outputs (fewer than R rows or columns to a
+    // grid edge), one per thread, with the stencil of their edge class.
+    // Edge columns (all 32 rows) first, then edge rows (the other columns).
+    float eb_v = -INFINITY;
+    long long eb_i = -1;
+    {
+        int ecol[2 * R], erow[2 * R];
+        int nec = 0, ner = 0;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            if (c0 + k < R && c0 + k < g2) ecol[nec++] = c0 + k;                 // left edge
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int c = g2 - R + k;
+            if (c >= R && c >= c0 && c < c0 + kColsPerBlock) ecol[nec++] = c;     // right edge
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            if (r0 + k < R && r0 + k < g1) erow[ner++] = r0 + k;                 // top edge
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int r = g1 - R + k;
+            if (r >= R && r >= r0 && r < r0 + kRowsPerBlock) erow[ner++] = r;     // bottom edge
+        }
+        const int rows_here = min(kRowsPerBlock, g1 - r0);
+        const int n1 = nec * rows_here, n2 = ner * kColsPerBlock;
+        for (int t = threadIdx.x; t < n1 + n2; t += blockDim.x) {
+            int r, c;
+            if (t < n1) { c = ecol[t / rows_here]; r = r0 + t % rows_here; }
+            else {
+                r = erow[(t - n1) / kColsPerBlock];
+                c = c0 + (t - n1) % kColsPerBlock;
+                if (c >= g2 || c < R || c > g2 - 1 - R) continue;                // edge columns done above
+            }
+            const float* w = w32 + static_cast<int64_t>(cls(r, g1, R) * ncls + cls(c, g2, R)) * kMaxTaps;
+            float acc = 0.0f;
+#pragma unroll
+            for (int dx = 0; dx < T; ++dx)
+#pragma unroll
+                for (int dy = 0; dy < T; ++dy)
+                    acc = fmaf(__ldg(&w[dx * T + dy]), tile[r - r0 + dx][c - c0 + dy], acc);
+            const long long idx = static_cast<long long>(r) * g2 + c;
+            if (O) O[idx] = f2d_bits(acc);
+            if (acc > eb_v || (acc == eb_v && idx < eb_i)) { eb_v = acc; eb_i = idx; }
+        }
+    }
+    best = fmaxf(best, eb_v);
+    // Argmax: the block's largest value first (max reductions only), then the
+    // lowest index holding it, searched by the few threads that hold it.
+    {
+        float m = best;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0) sm_max[threadIdx.x >> 5] = m;
+        if (threadIdx.x == 0) sm_idx = -1;
+        __syncthreads();
+        float bm = sm_max[0];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) bm = fmaxf(bm, sm_max[w]);
+        if (best == bm && bm > -INFINITY) {
+            long long cand = (eb_v == bm) ? eb_i : -1;
+#pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const bool row_int = orow + i >= R && orow + i <= g1 - 1 - R;
-                const long long idx0 = static_cast<long long>(orow + i) * g2 + ocol;
-                unsigned long long o[4];
-    #pragma unroll
-                for (int j = 0; j < 4; ++j) o[j] = f2d_bits(acc[i][j]);
-                if (O && row_int) {
-                    if (vec && all_cols) {
-                        ulonglong2* dst = reinterpret_cast<ulonglong2*>(O + idx0);
-                        dst[0] = make_ulonglong2(o[0], o[1]);
-                        dst[1] = make_ulonglong2(o[2], o[3]);
-                    } else {
-    #pragma unroll
-                        for (int j = 0; j < 4; ++j) if (col_int[j]) O[idx0 + j] = o[j];
-                    }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const bool v = row_int && ocol + j >= R && ocol + j <= g2 - 1 - R && keep[i][j] == bm;
+                    const long long idx = static_cast<long long>(orow + i) * g2 + ocol + j;
+                    if (v && (cand < 0 || idx < cand)) cand = idx;
                 }
-    #pragma unroll
-                for (int j = 0; j < 4; ++j) best = fmaxf(best, (row_int && col_int[j]) ? acc[i][j] : -INFINITY);
             }
-            // keep the patch for the index search of the winning threads
-    #pragma unroll
-            for (int i = 0; i < 4; ++i)
-    #pragma unroll
-                for (int j = 0; j < 4; ++j) keep[i][j] = acc[i][j];
+            if (cand >= 0) atomicMin(reinterpret_cast<unsigned long long*>(&sm_idx), static_cast<unsigned long long>(cand));
         }
-        // Phase B: the block's edge outputs (fewer than R rows or columns to a
-        // grid edge), one per thread, with the stencil of their edge class.
-        // Edge columns (all 32 rows) first, then edge rows (the other columns).
-        float eb_v = -INFINITY;
-        long long eb_i = -1;
-        {
-            int ecol[2 * R], erow[2 * R];
-            int nec = 0, ner = 0;
-    #pragma unroll
-            for (int k = 0; k < R; ++k) {
-                if (c0 + k < R && c0 + k < g2) ecol[nec++] = c0 + k;                 // left edge
-            }
-    #pragma unroll
-            for (int k = 0; k < R; ++k) {
-                const int c = g2 - R + k;
-                if (c >= R && c >= c0 && c < c0 + kColsPerBlock) ecol[nec++] = c;     // right edge
-            }
-    #pragma unroll
-            for (int k = 0; k < R; ++k) {
-                if (r0 + k < R && r0 + k < g1) erow[ner++] = r0 + k;                 // top edge
-            }
-    #pragma unroll
-            for (int k = 0; k < R; ++k) {
-                const int r = g1 - R + k;
-                if (r >= R && r >= r0 && r < r0 + kRowsPerBlock) erow[ner++] = r;     // bottom edge
-            }
-            const int rows_here = min(kRowsPerBlock, g1 - r0);
-            const int n1 = nec * rows_here, n2 = ner * kColsPerBlock;
-            for (int t = threadIdx.x; t < n1 + n2; t += blockDim.x) {
-                int r, c;
-                if (t < n1) { c = ecol[t / rows_here]; r = r0 + t % rows_here; }
-                else {
-                    r = erow[(t - n1) / kColsPerBlock];
-                    c = c0 + (t - n1) % kColsPerBlock;
-                    if (c >= g2 || c < R || c > g2 - 1 - R) continue;                // edge columns done above
-                }
-                const float* w = w32 + static_cast<int64_t>(cls(r, g1, R) * ncls + cls(c, g2, R)) * kMaxTaps;
-                float acc = 0.0f;
-    #pragma unroll
-                for (int dx = 0; dx < T; ++dx)
-    #pragma unroll
-                    for (int dy = 0; dy < T; ++dy)
-                        acc = fmaf(__ldg(&w[dx * T + dy]), tile[r - r0 + dx][c - c0 + dy], acc);
-                const long long idx = static_cast<long long>(r) * g2 + c;
-                if (O) O[idx] = f2d_bits(acc);
-                if (acc > eb_v || (acc == eb_v && idx < eb_i)) { eb_v = acc; eb_i = idx; }
-            }
-        }
-        best = fmaxf(best, eb_v);
-        // Argmax: the block's largest value first (max reductions only), then the
-        // lowest index holding it, searched by the few threads that hold it.
-        {
-            float m = best;
-    #pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-            if ((threadIdx.x & 31) == 0) sm_max[threadIdx.x >> 5] = m;
-            if (threadIdx.x == 0) sm_idx = -1;
-            __syncthreads();
-            float bm = sm_max[0];
-    #pragma unroll
-            for (int w = 1; w < 8; ++w) bm = fmaxf(bm, sm_max[w]);
-            if (best == bm && bm > -INFINITY) {
-                long long cand = (eb_v == bm) ? eb_i : -1;
-    #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const bool row_int = orow + i >= R && orow + i <= g1 - 1 - R;
-    #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const bool v = row_int && ocol + j >= R && ocol + j <= g2 - 1 - R && keep[i][j] == bm;
-                        const long long idx = static_cast<long long>(orow + i) * g2 + ocol + j;
-                        if (v && (cand < 0 || idx < cand)) cand = idx;
-                    }
-                }
-                if (cand >= 0) atomicMin(reinterpret_cast<unsigned long long*>(&sm_idx), static_cast<unsigned long long>(cand));
-            }
-            __syncthreads();
-            best_i = sm_idx;
-            best = bm;
-        }
-        if (threadIdx.x == 0) {
-            part_v[static_cast<int64_t>(s) * nb + b] = best_i >= 0 ? order_key(f2d_bits(best)) : 0ull;
-            part_i[static_cast<int64_t>(s) * nb + b] = best_i;
-        }
-        if constexpr (RAW) {
-            unsigned long long raw_k = raw.key;
-            long long raw_i = raw.idx;
-            block_amax(raw_k, raw_i, sv, si);
-            if (threadIdx.x == 0) { rpart_v[static_cast<int64_t>(s) * nb + b] = raw_k; rpart_i[static_cast<int64_t>(s) * nb + b] = raw_i; }
-        }
-        __syncthreads();                                    // tile and stage[buf] are free again
+        __syncthreads();
+        best_i = sm_idx;
+        best = bm;
+    }
+    const int nb = gridDim.x * gridDim.y;
+    const int b = blockIdx.y * gridDim.x + blockIdx.x;
+    if (threadIdx.x == 0) {
+        part_v[static_cast<int64_t>(s) * nb + b] = best_i >= 0 ? order_key(f2d_bits(best)) : 0ull;
+        part_i[static_cast<int64_t>(s) * nb + b] = best_i;
+    }
+    if constexpr (RAW) {
+        unsigned long long raw_k = raw.key;
+        long long raw_i = raw.idx;
+        block_amax(raw_k, raw_i, sv, si);
+        if (threadIdx.x == 0) { rpart_v[static_cast<int64_t>(s) * nb + b] = raw_k; rpart_i[static_cast<int64_t>(s) * nb + b] = raw_i; }
     }
 }
 
@@ -555,36 +508,6 @@ int blocks_per_scen(int g1, int g2) {
     return ((g2 + kColsPerBlock - 1) / kColsPerBlock) * ((g1 + kRowsPerBlock - 1) / kRowsPerBlock);
 }
 
-template <int R, bool RAW>
-cudaError_t launch_smooth2d_t(int n_scen, int g1, int g2, const unsigned long long* vb, const float* w,
-                              unsigned long long* ob, unsigned long long* pv, long long* pi,
-                              unsigned long long* rpv, long long* rpi, cudaStream_t stream) {
-    const size_t smem = Smooth2dShape<R>::kSmem;
-    cudaError_t e = cudaFuncSetAttribute(smooth2d_kernel<R, RAW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, bps = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, smooth2d_kernel<R, RAW>, 256, smem);
-    if (e != cudaSuccess) return e;
-    const long long total = static_cast<long long>(n_scen) * blocks_per_scen(g1, g2);
-    const long long grid = std::max<long long>(1, std::min<long long>(total, static_cast<long long>(std::max(bps, 1)) * sms));
-    smooth2d_kernel<R, RAW><<<static_cast<unsigned>(grid), 256, smem, stream>>>(vb, n_scen, g1, g2, w, ob, pv, pi, rpv, rpi);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_smooth2d(int R, bool raw, int n_scen, int g1, int g2, const unsigned long long* vb,
-                            const float* w, unsigned long long* ob, unsigned long long* pv, long long* pi,
-                            unsigned long long* rpv, long long* rpi, cudaStream_t stream) {
-    if (R == 1) return raw ? launch_smooth2d_t<1, true>(n_scen, g1, g2, vb, w, ob, pv, pi, rpv, rpi, stream)
-                           : launch_smooth2d_t<1, false>(n_scen, g1, g2, vb, w, ob, pv, pi, rpv, rpi, stream);
-    if (R == 2) return raw ? launch_smooth2d_t<2, true>(n_scen, g1, g2, vb, w, ob, pv, pi, rpv, rpi, stream)
-                           : launch_smooth2d_t<2, false>(n_scen, g1, g2, vb, w, ob, pv, pi, rpv, rpi, stream);
-    return raw ? launch_smooth2d_t<3, true>(n_scen, g1, g2, vb, w, ob, pv, pi, rpv, rpi, stream)
-               : launch_smooth2d_t<3, false>(n_scen, g1, g2, vb, w, ob, pv, pi, rpv, rpi, stream);
-}
-
 }  // namespace
 
 size_t smooth_weight_count() {
@@ -620,8 +543,17 @@ cudaError_t smooth_argmax(int n_scen, int g1, int g2, const double* value, doubl
     const unsigned long long* vb = reinterpret_cast<const unsigned long long*>(value);
     unsigned long long* ob = reinterpret_cast<unsigned long long*>(smoothed);
     if (two_d) {
-        e = launch_smooth2d(R, raw_idx || raw_val, n_scen, g1, g2, vb, wbuf32, ob, pv, pi, rpv, rpi, stream);
-        if (e != cudaSuccess) return e;
+        dim3 grid((g2 + kColsPerBlock - 1) / kColsPerBlock, (g1 + kRowsPerBlock - 1) / kRowsPerBlock, n_scen);
+        const bool raw = raw_idx || raw_val;
+        if (raw) {
+            if (R == 1) smooth2d_kernel<1, true><<<grid, 256, 0, stream>>>(vb, g1, g2, wbuf32, ob, pv, pi, rpv, rpi);
+            else if (R == 2) smooth2d_kernel<2, true><<<grid, 256, 0, stream>>>(vb, g1, g2, wbuf32, ob, pv, pi, rpv, rpi);
+            else smooth2d_kernel<3, true><<<grid, 256, 0, stream>>>(vb, g1, g2, wbuf32, ob, pv, pi, rpv, rpi);
+        } else {
+            if (R == 1) smooth2d_kernel<1, false><<<grid, 256, 0, stream>>>(vb, g1, g2, wbuf32, ob, pv, pi, rpv, rpi);
+            else if (R == 2) smooth2d_kernel<2, false><<<grid, 256, 0, stream>>>(vb, g1, g2, wbuf32, ob, pv, pi, rpv, rpi);
+            else smooth2d_kernel<3, false><<<grid, 256, 0, stream>>>(vb, g1, g2, wbuf32, ob, pv, pi, rpv, rpi);
+        }
     } else {
         dim3 grid(nb, n_scen);
         const int n = g1 * g2;
