@@ -196,6 +196,24 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------ multi-replica runs
+def rank_keys(keys, rank):
+    """Stream keys of rank `rank`: each replica evaluates its own independent
+    copy of the grid (weak scaling; rank 0 keeps the workload's keys)."""
+    return np.asarray(keys, dtype=np.uint64) + np.uint64(rank * 1_000_003)
+
+
+def max_over_ranks(t, device):
+    """The slowest rank's time (the only collective besides the barrier)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return t
+    x = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(x, op=dist.ReduceOp.MAX)
+    return float(x.item())
+
+
 # ------------------------------------------------------------ our arm
 def traffic_record(tiles):
     """DRAM bytes of one sampling launch of `tiles` tiles, from the committed
@@ -253,8 +271,7 @@ def run_ours(args, rank, world):
     ctx = pkg.Context(dev.index)
     prob = workloads.c2()
     if world > 1:
-        # weak scaling: each rank evaluates its own independent copy of the grid
-        prob.keys = prob.keys + np.uint64(rank * 1_000_003)
+        prob.keys = rank_keys(prob.keys, rank)
     dp = pkg.DeviceProblem.from_workload(prob)
     jac = torch.as_tensor(prob.jac_packed(), dtype=torch.float64, device=dev)
     plan = pkg.Plan(ctx, dp, grad=True, k=4, autotune=True, graph=True, timing=True)
@@ -294,11 +311,7 @@ def run_ours(args, rank, world):
     wall = time.perf_counter() - wall0
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_total = sum(step_ms) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
+    t_total = max_over_ranks(t_total, dev)
     clk = clocks.stop() if rank == 0 else None
     ctx.sync_status()
 
