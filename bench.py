@@ -398,6 +398,84 @@ def run_ours(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def c3_batched_vs_per_design(pkg, ctx, n_sub=512):
+    """C3 (256 scenarios, d = 3..10, 38k designs): the whole batch in one
+    persistent graph-replayed launch, and on an evenly spaced subsample the
+    same designs as one launch each; hits must agree exactly."""
+    import torch
+
+    import workloads
+    prob = workloads.c3()
+    stream = torch.cuda.current_stream()
+    dp = pkg.DeviceProblem.from_workload(prob)
+    plan = pkg.Plan(ctx, dp, autotune=True, graph=True)
+    plan.eval(1, stream=stream)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    full = plan.eval(2, stream=stream)
+    b.record(stream)
+    b.synchronize()
+    full_ms = a.elapsed_time(b)
+    full_hits = full["hits"].cpu().numpy()
+    plan.close()
+    idx = np.linspace(0, prob.n_design - 1, n_sub).astype(int)
+    sub = prob.subset(idx)
+    sdp = pkg.DeviceProblem.from_workload(sub)
+    batched = pkg.Plan(ctx, sdp, graph=True)
+    batched.eval(2, stream=stream)
+    singles = []
+    for j in range(n_sub):
+        one = prob.subset([int(idx[j])])
+        odp = pkg.DeviceProblem.from_workload(one)
+        singles.append((pkg.Plan(ctx, odp), odp))
+    torch.cuda.synchronize()
+    a.record(stream)
+    sb = batched.eval(2, stream=stream)
+    b.record(stream)
+    b.synchronize()
+    batched_ms = a.elapsed_time(b)
+    outs = []
+    a.record(stream)
+    for pl, _ in singles:
+        outs.append(pl.eval(2, stream=stream, out={"hits": torch.empty(1, dtype=torch.int64, device="cuda"),
+                                                  "p": torch.empty(1, dtype=torch.float64, device="cuda"),
+                                                  "se": torch.empty(1, dtype=torch.float64, device="cuda")}))
+    b.record(stream)
+    b.synchronize()
+    single_ms = a.elapsed_time(b)
+    ctx.sync_status()
+    single_hits = np.array([int(o["hits"].item()) for o in outs])
+    equal = bool(np.array_equal(single_hits, sb["hits"].cpu().numpy())
+                 and np.array_equal(single_hits, full_hits[idx]))
+    for pl, _ in singles:
+        pl.close()
+    batched.close()
+    draws_sub = float(sub.n_draws.astype(np.float64).sum())
+    return {"designs": int(prob.n_design), "draws": float(prob.total_draws()), "batched_ms": full_ms,
+            "batched_draw_evals_per_s": prob.total_draws() / (full_ms / 1e3),
+            "subsample": {"designs": n_sub, "draws": draws_sub, "one_launch_ms": batched_ms,
+                          "per_design_launches_ms": single_ms, "speedup": single_ms / batched_ms,
+                          "hits_bit_identical": equal}}
+
+
+def c4_search(pkg, ctx):
+    """Gradient-driven search on the d=10 grid's design space (projected Adam,
+    likelihood-ratio adjoint, common random numbers)."""
+    import torch
+
+    import workloads
+    from paper_2005_10494_gb300 import search
+    prob = workloads.c4(g1=2, g2=2, n_draws=10)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x, p_hat, hist = search.gradient_search(ctx, lambda v: workloads.design_at("c4", v[0], v[1]), prob.sigmas[0],
+                                            x0=(0.5, 0.5), lo=(0.05, 0.2), hi=(0.95, 0.8), n_draws=10_000_000,
+                                            steps=120)
+    dt = time.perf_counter() - t0
+    return {"steps": 120, "draws_per_step": 10_000_000, "seconds": dt, "q": float(x[0]), "a": float(x[1]),
+            "p_hat": p_hat}
+
+
 def run_extras(pkg, ctx, c2):
     import torch
 
@@ -417,6 +495,10 @@ def run_extras(pkg, ctx, c2):
     r20g, _ = kernel_rate(pkg, ctx, c5, grad=True, reps=1)
     ex["d20"] = {"fwd": r20f, "adj": r20g, "adjoint_overhead": r20f / r20g,
                  "fwd_op_frac": r20f * ops_per_draw(20, False) / (152 * LANES * SM_MAX_MHZ * 1e6)}
+    # batched uneven dimensions: one persistent launch vs one launch per design
+    ex["c3"] = c3_batched_vs_per_design(pkg, ctx)
+    # d=10 gradient search (120 adjoint launches of 1e7 draws)
+    ex["c4_search"] = c4_search(pkg, ctx)
     # smoothing at scale: 4096 scenarios x 256 x 256 FP64 grids
     S, G = 4096, 256
     v = torch.rand(S * G * G, dtype=torch.float64, device="cuda")
