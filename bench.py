@@ -244,7 +244,7 @@ def kernel_rate(pkg, ctx, prob, grad, reps=2, h=0.01):
     """Draw-evals/s of the sampling kernel alone on one workload (CUDA events)."""
     import torch
     dp = pkg.DeviceProblem.from_workload(prob)
-    plan = pkg.Plan(ctx, dp, grad=grad, k=4 if grad else 0, timing=True)
+    plan = pkg.Plan(ctx, dp, grad=grad, k=4 if grad else 0, timing=True, autotune=True)
     jac = torch.as_tensor(prob.jac_packed(), dtype=torch.float64, device="cuda") if grad else None
     best = 1e30
     for r in range(reps + 1):
