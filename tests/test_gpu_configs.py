@@ -115,3 +115,15 @@ def test_c3_persistent_vs_per_design(ctx):
         assert int(single["hits"][0]) == int(batched["hits"][j])
     ora = oracle_same_stream(prob, 0, idx[:12])
     assert_discordance(batched["hits"], ora, idx[:12])
+
+
+def test_paper_optimal_designs_on_gpu(ctx):
+    # the paper's reported optima (Sec. 3) estimated on the GPU with the prior
+    # folded into the sampling law: within 5 SE of the exact value, and the
+    # printed powers (a) 0.6847, (c) 0.977 within the oracle pins' tolerances
+    prob = workloads.paper_optima(n_draws=10_000_000)
+    out = run(ctx, prob, seed=0)
+    exact = [1.0 - quad.orthant_dense(prob.t(j), prob.sigmas[j]) for j in range(3)]
+    assert_band(out["p"], exact, 10_000_000, [0, 1, 2])
+    assert abs(out["p"][0] - 0.6847) <= 5e-3
+    assert abs(out["p"][2] - 0.977) <= 1e-3

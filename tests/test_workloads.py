@@ -93,3 +93,17 @@ def test_c1_surface_has_interior_optimum():
     k = int(np.argmax(vals))
     assert 0 < k < 100
     assert min(vals) > 0.4 and max(vals) < 0.99
+
+
+def test_paper_designs_match_oracle_collapse():
+    # the input module's sampling law of the paper's designs (Eq. 1, 3, 10)
+    # equals the oracle's independent restatement
+    p = workloads.paper_optima(n_draws=10)
+    r_list = [[1.0], [1.0, 0.365], [1.0, 0.446, 0.168]]
+    I3s = [127.0, 211.0, 211.0]
+    d0s = [lambda r: 0.25 + 0.0 * r, lambda r: 0.3 - 0.1 * r, lambda r: 0.8 - 0.6 * r]
+    for j in range(3):
+        r = np.array(r_list[j])
+        mu, C = design.collapsed_prior(r, I3s[j], d0s[j](r))
+        np.testing.assert_allclose(p.mus[j], mu, rtol=1e-14, atol=0)
+        np.testing.assert_allclose(p.sigmas[j], C, rtol=1e-14, atol=1e-15)

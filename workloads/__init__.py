@@ -325,6 +325,48 @@ def c5_subsample(n=64, total=4096, seed=0):
     return np.sort(np.random.default_rng(seed).choice(total, n, replace=False))
 
 
+def nested_sigma(r):
+    """Correlation of the Z statistics of nested populations (Eq. 1):
+    corr(X_k, X_l) = sqrt(r_l / r_k) for r_l <= r_k."""
+    r = np.asarray(r, dtype=np.float64)
+    lo, hi = np.minimum.outer(r, r), np.maximum.outer(r, r)
+    return np.sqrt(lo / hi)
+
+
+def paper_design(r, alpha, I3, delta0, prior_sd_scale=20.0):
+    """Sampling law of one of the paper's designs with its Gaussian prior on
+    the effect sizes (Eq. 1, 3, 10) folded in: X = X0 + S Delta with
+    X0 ~ N(0, Sigma(r)), Delta ~ N(theta, Sigma_p), S = diag(sqrt(r_i I3)), so
+    X ~ N(S theta, Sigma(r) + S Sigma_p S).  theta = -log(1 - Delta0),
+    Sigma_p = Sigma(r) * (sigma sigma^T) with sigma_i = 1/sqrt(20 r_i), and the
+    thresholds are b_i = Z_{1 - alpha_i}.  Returns (mean, covariance, b)."""
+    r = np.asarray(r, dtype=np.float64)
+    Sig = nested_sigma(r)
+    theta = -np.log1p(-np.asarray(delta0, dtype=np.float64))
+    sd = 1.0 / np.sqrt(prior_sd_scale * r)
+    S = np.sqrt(r * I3)
+    cov = Sig + np.outer(S, S) * Sig * np.outer(sd, sd)
+    return S * theta, cov, special.ndtri(1.0 - np.asarray(alpha, dtype=np.float64))
+
+
+def paper_optima(n_draws=10_000_000):
+    """The optimal designs the paper reports for its biomarker conditions
+    (Sec. 3): (a) no biomarker effect, (b) weak, (c) strong; one scenario
+    each (the covariance depends on the design), keys 0, 1, 2."""
+    cases = [([1.0], [0.025], 127.0, [0.25]),
+             ([1.0, 0.365], [0.0163, 0.0107], 211.0, [0.3 - 0.1, 0.3 - 0.1 * 0.365]),
+             ([1.0, 0.446, 0.168], [0.00194, 0.0135, 0.0133], 211.0,
+              [0.8 - 0.6 * 1.0, 0.8 - 0.6 * 0.446, 0.8 - 0.6 * 0.168])]
+    sig, mus, bs = [], [], []
+    for r, alpha, I3v, d0 in cases:
+        m, C, b = paper_design(r, alpha, I3v, d0)
+        sig.append(C)
+        mus.append(m)
+        bs.append(b)
+    return Problem("paper-optima", sig, [0, 1, 2], mus, bs, [n_draws] * 3, [0, 1, 2],
+                   structures=[{"kind": "dense"}] * 3)
+
+
 def design_at(config, q, a, scenario=0):
     """mu, b, dt/dtheta of one off-grid design of a grid config (for searches)."""
     if config == "c4":
