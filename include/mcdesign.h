@@ -103,6 +103,16 @@ mcd_status mcd_sync_status(mcd_ctx* ctx, mcd_stream stream);
 #define MCD_PLAN_GRAPH     4  /* replay launches from a captured CUDA graph    */
 #define MCD_PLAN_FP64      8  /* all-FP64 sampling (normals, L z, sums); one d */
 #define MCD_PLAN_TIMING   16  /* record CUDA events around the sampling kernels */
+#define MCD_PLAN_SHARED   32  /* shared-draw kernel for common-random-number groups */
+
+/* MCD_PLAN_SHARED: designs with equal (design_scen, key, draw_begin, n_draws)
+ * see the same draws (common random numbers).  Groups of at least
+ * MCD_SHARED_MIN such designs are evaluated by the shared-draw kernel, which
+ * makes each draw once per block and tests it against every design of the
+ * group: hit counts are bit-identical to the per-design kernel, gradient
+ * sums equal up to the order of FP32 additions.  Smaller groups keep the
+ * per-design kernel.  Not with MCD_PLAN_FP64 (MCD_EUNSUPPORTED). */
+#define MCD_SHARED_MIN    32
 
 /* Plan a problem.  Reads the HOST arrays (copied), keeps the DEVICE
  * pointers Sigma, mu, b (their contents are read at each launch), uploads

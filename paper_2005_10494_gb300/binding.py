@@ -16,7 +16,8 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "mcdesign.h")
 
 MCD_OK, MCD_EINVAL, MCD_ENOTSPD, MCD_ECUDA, MCD_ENOMEM, MCD_EUNSUPPORTED, MCD_ENAN = 0, 1, 2, 3, 5, 6, 7
 MCD_ANY_EXCEEDS, MCD_ALL_BELOW = 0, 1
-MCD_PLAN_GRAD, MCD_PLAN_AUTOTUNE, MCD_PLAN_GRAPH, MCD_PLAN_FP64, MCD_PLAN_TIMING = 1, 2, 4, 8, 16
+MCD_PLAN_GRAD, MCD_PLAN_AUTOTUNE, MCD_PLAN_GRAPH, MCD_PLAN_FP64, MCD_PLAN_TIMING, MCD_PLAN_SHARED = 1, 2, 4, 8, 16, 32
+MCD_SHARED_MIN = 32
 MCD_MAX_D = 20
 
 _c_i32p = ctypes.POINTER(ctypes.c_int32)
@@ -202,10 +203,12 @@ def _trim(out, J, n):
 class Plan:
     """mcd_plan_create / mcd_plan_eval / mcd_plan_grad."""
 
-    def __init__(self, ctx, prob, grad=False, k=0, autotune=False, graph=False, fp64=False, timing=False):
+    def __init__(self, ctx, prob, grad=False, k=0, autotune=False, graph=False, fp64=False, timing=False,
+                 shared=False):
         self.ctx, self.prob, self.k = ctx, prob, k
         flags = (MCD_PLAN_GRAD if grad else 0) | (MCD_PLAN_AUTOTUNE if autotune else 0) \
-            | (MCD_PLAN_GRAPH if graph else 0) | (MCD_PLAN_FP64 if fp64 else 0) | (MCD_PLAN_TIMING if timing else 0)
+            | (MCD_PLAN_GRAPH if graph else 0) | (MCD_PLAN_FP64 if fp64 else 0) | (MCD_PLAN_TIMING if timing else 0) \
+            | (MCD_PLAN_SHARED if shared else 0)
         h = ctypes.c_void_p()
         ctx.check(ctx.lib.mcd_plan_create(ctx.handle, ctypes.byref(prob.c), flags, k, ctypes.byref(h)))
         self.handle = h

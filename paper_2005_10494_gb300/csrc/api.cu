@@ -9,6 +9,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "mcd_internal.cuh"
@@ -50,6 +51,16 @@ struct Segment {
     int blocks_per_sm = 0;
 };
 
+// One launch of the shared-draw kernel: the shared tiles
+// [tile_begin, tile_begin + n_tiles) of dimension d.
+struct SharedSeg {
+    int d = 0;
+    int64_t tile_begin = 0, n_tiles = 0;
+    int64_t tile_draws = 0;
+    int grid = 0;
+    int blocks_per_sm = 0;
+};
+
 // Which tiles a plan keeps (the autotuner times filtered plans).
 struct TileFilter {
     int d_lo = 1, d_hi = MCD_MAX_D;
@@ -86,6 +97,8 @@ struct mcd_plan {
     std::vector<int> seg_of_d;       // segment index of each dimension, -1 if none
     std::vector<int64_t> tile_draws_of_d;  // per d
     int64_t n_tiles = 0;
+    std::vector<SharedSeg> ssegs;    // shared-draw launches, after the per-design ones
+    int64_t n_shared_tiles = 0;
     int batches = 1;
     const double* Sigma = nullptr;
     const double* mu = nullptr;
@@ -103,7 +116,9 @@ struct mcd_plan {
     uint64_t* d_batch_draws = nullptr;
     unsigned long long* d_hits = nullptr;
     unsigned long long* d_gacc = nullptr;
-    unsigned int* d_ticket = nullptr;  // one tile counter per segment
+    unsigned int* d_ticket = nullptr;  // one tile counter per segment (per-design, then shared)
+    SharedTile* d_stiles = nullptr;
+    uint32_t* d_slist = nullptr;       // designs of the shared tiles, chunk by chunk
     size_t gacc_len = 0;
     std::vector<void*> owned;
     // CUDA graphs, one per launch kind (0 eval, 1 grad)
@@ -233,6 +248,25 @@ mcd_status plan_build(mcd_ctx* ctx, const mcd_problem* pr, int32_t flags, int32_
     pl->mu = pr->mu;
     pl->b = pr->b;
     const int S = pl->S, J = pl->J;
+    const bool grad_kernel = (flags & MCD_PLAN_GRAD) != 0;
+
+    // common-random-number groups for the shared-draw kernel
+    std::vector<char> is_shared(J, 0);
+    std::vector<std::vector<int>> groups;
+    if (flags & MCD_PLAN_SHARED) {
+        if (pl->fp64) return fail(ctx, MCD_EUNSUPPORTED, "MCD_PLAN_SHARED is not available with MCD_PLAN_FP64");
+        std::map<std::tuple<int, uint64_t, uint64_t, uint64_t>, std::vector<int>> by;
+        for (int j = 0; j < J; ++j) {
+            const uint64_t begin = pr->draw_begin ? pr->draw_begin[j] : 0;
+            if (pr->n_draws[j] == 0) continue;
+            by[std::make_tuple(pr->design_scen[j], pr->key[j], begin, pr->n_draws[j])].push_back(j);
+        }
+        for (auto& kv : by) {
+            if (static_cast<int>(kv.second.size()) < MCD_SHARED_MIN) continue;
+            for (int j : kv.second) is_shared[j] = 1;
+            groups.push_back(std::move(kv.second));
+        }
+    }
 
     std::vector<int64_t> sig_off(S), L_off(S);
     std::vector<int32_t> scen_d(pr->scen_d, pr->scen_d + S);
@@ -246,7 +280,8 @@ mcd_status plan_build(mcd_ctx* ctx, const mcd_problem* pr, int32_t flags, int32_
     // segments: all d <= kMixedMaxD in one launch (the mixed kernel when
     // they differ), each larger d in its own launch
     std::vector<int> present(MCD_MAX_D + 1, 0);
-    for (int j = 0; j < J; ++j) present[scen_d[pr->design_scen[j]]] = 1;
+    for (int j = 0; j < J; ++j)
+        if (!is_shared[j]) present[scen_d[pr->design_scen[j]]] = 1;
     int n_small = 0, small_lo = MCD_MAX_D + 1, small_hi = 0;
     for (int d = 1; d <= kMixedMaxD; ++d)
         if (present[d]) { ++n_small; small_lo = std::min(small_lo, d); small_hi = d; }
@@ -271,7 +306,6 @@ mcd_status plan_build(mcd_ctx* ctx, const mcd_problem* pr, int32_t flags, int32_
         pl->seg_of_d[d] = static_cast<int>(pl->segs.size());
         pl->segs.push_back(sg);
     }
-    const bool grad_kernel = (flags & MCD_PLAN_GRAD) != 0;
     pl->tile_draws_of_d.assign(MCD_MAX_D + 1, 0);
     for (auto& sg : pl->segs) {
         {
@@ -296,10 +330,49 @@ mcd_status plan_build(mcd_ctx* ctx, const mcd_problem* pr, int32_t flags, int32_
         designs[j].d = d;
         vo += d;
         const int64_t T = pl->tile_draws_of_d[d];
-        const bool keep = (j % filt.stride == 0) && d >= filt.d_lo && d <= filt.d_hi;
+        const bool keep = !is_shared[j] && (j % filt.stride == 0) && d >= filt.d_lo && d <= filt.d_hi;
         tiles_of[j] = keep ? static_cast<int64_t>((n_draws[j] + T - 1) / T) : 0;
         total_tiles += tiles_of[j];
         max_tiles = std::max(max_tiles, tiles_of[j]);
+    }
+
+    // shared-draw schedule: per dimension one launch; a group is cut into
+    // chunks of at most kSharedThreads * (designs per thread) designs of
+    // balanced size, and its draw range into tiles of whole batches sized so
+    // that each launch has about 16 tiles per resident block
+    struct SChunk { int g; size_t first, cnt; };
+    std::vector<SChunk> chunks;
+    std::vector<int64_t> stile_draws(MCD_MAX_D + 1, 0);
+    pl->ssegs.clear();
+    {
+        std::vector<double> chunk_draws(MCD_MAX_D + 1, 0.0);
+        for (size_t g = 0; g < groups.size(); ++g) {
+            const int d = scen_d[pr->design_scen[groups[g][0]]];
+            const size_t cap = static_cast<size_t>(kSharedThreads) * shared_designs_per_thread(d, grad_kernel);
+            const size_t m = groups[g].size(), nch = (m + cap - 1) / cap, per = (m + nch - 1) / nch;
+            for (size_t c = 0; c < m; c += per) chunks.push_back({static_cast<int>(g), c, std::min(per, m - c)});
+            chunk_draws[d] += static_cast<double>(nch) * static_cast<double>(n_draws[groups[g][0]]);
+        }
+        for (int d = 1; d <= MCD_MAX_D; ++d) {
+            if (chunk_draws[d] == 0.0) continue;
+            SharedSeg sg;
+            sg.d = d;
+            int bps = 0;
+            cudaError_t e = shared_occupancy(d, grad_kernel, &bps);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "occupancy query");
+            sg.blocks_per_sm = std::max(1, bps);
+            const double bd = shared_batch_draws(d);
+            const double want = chunk_draws[d] / (16.0 * ctx->sm_count * sg.blocks_per_sm);
+            const int64_t mult = std::max<int64_t>(1, std::min<int64_t>(256, std::llround(want / bd)));
+            sg.tile_draws = mult * static_cast<int64_t>(bd);
+            stile_draws[d] = sg.tile_draws;
+            pl->ssegs.push_back(sg);
+        }
+        for (const SChunk& c : chunks) {
+            const int j0 = groups[c.g][0];
+            const int64_t T = stile_draws[scen_d[pr->design_scen[j0]]];
+            max_tiles = std::max<int64_t>(max_tiles, static_cast<int64_t>((n_draws[j0] + T - 1) / T));
+        }
     }
     if (total_tiles >= (1ll << 31)) return fail(ctx, MCD_EINVAL, "too many tiles (reduce n_draws)");
     pl->n_tiles = total_tiles;
@@ -327,6 +400,53 @@ mcd_status plan_build(mcd_ctx* ctx, const mcd_problem* pr, int32_t flags, int32_
             tiles.push_back(tr);
         }
     }
+    // shared tiles and their design lists
+    std::vector<SharedTile> stiles;
+    std::vector<uint32_t> slist;
+    for (const SChunk& c : chunks) {
+        const std::vector<int>& gr = groups[c.g];
+        const int j0 = gr[c.first];
+        const int d = scen_d[pr->design_scen[j0]];
+        const int64_t T = stile_draws[d];
+        const uint64_t begin = pr->draw_begin ? pr->draw_begin[j0] : 0;
+        const uint64_t n = n_draws[j0];
+        const uint32_t off = static_cast<uint32_t>(slist.size());
+        for (size_t q = 0; q < c.cnt; ++q) slist.push_back(static_cast<uint32_t>(gr[c.first + q]));
+        const int64_t ranges = static_cast<int64_t>((n + T - 1) / T);
+        for (int64_t r = 0; r < ranges; ++r) {
+            SharedTile st;
+            st.start = begin + static_cast<uint64_t>(r) * T;
+            st.n = static_cast<uint32_t>(std::min<uint64_t>(n - static_cast<uint64_t>(r) * T, static_cast<uint64_t>(T)));
+            st.key = pr->key[j0];
+            st.list_off = off;
+            st.list_cnt = static_cast<uint32_t>(c.cnt);
+            st.batch = static_cast<uint32_t>(r % B);
+            st.scen = pr->design_scen[j0];
+            st.pad = 0;
+            for (size_t q = 0; q < c.cnt; ++q)
+                batch_draws[static_cast<size_t>(gr[c.first + q]) * B + st.batch] += st.n;
+            stiles.push_back(st);
+        }
+    }
+    if (static_cast<int64_t>(stiles.size()) + total_tiles >= (1ll << 31))
+        return fail(ctx, MCD_EINVAL, "too many tiles (reduce n_draws)");
+    std::stable_sort(stiles.begin(), stiles.end(), [&](const SharedTile& a, const SharedTile& c) {
+        const int da = scen_d[a.scen], dc = scen_d[c.scen];
+        if (da != dc) return da < dc;
+        return static_cast<double>(a.list_cnt) * a.n > static_cast<double>(c.list_cnt) * c.n;
+    });
+    {
+        int64_t pos = 0;
+        for (SharedSeg& sg : pl->ssegs) {
+            sg.tile_begin = pos;
+            while (pos < static_cast<int64_t>(stiles.size()) && scen_d[stiles[pos].scen] == sg.d) ++pos;
+            sg.n_tiles = pos - sg.tile_begin;
+            const int64_t g = static_cast<int64_t>(sg.blocks_per_sm) * ctx->sm_count;
+            sg.grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, sg.n_tiles)));
+        }
+    }
+    pl->n_shared_tiles = static_cast<int64_t>(stiles.size());
+
     // by segment, and within a segment the costliest tiles first: the
     // dynamic ticket then leaves only small tiles for the tail
     std::stable_sort(tiles.begin(), tiles.end(), [&](const TileRec& a, const TileRec& c) {
@@ -357,7 +477,10 @@ mcd_status plan_build(mcd_ctx* ctx, const mcd_problem* pr, int32_t flags, int32_
     if ((st = plan_alloc(pl, &pl->d_n_draws, J)) != MCD_OK) return st;
     if ((st = plan_alloc(pl, &pl->d_batch_draws, batch_draws.size())) != MCD_OK) return st;
     if ((st = plan_alloc(pl, &pl->d_hits, J)) != MCD_OK) return st;
-    if ((st = plan_alloc(pl, &pl->d_ticket, std::max<size_t>(1, pl->segs.size()))) != MCD_OK) return st;
+    if ((st = plan_alloc(pl, &pl->d_ticket, std::max<size_t>(1, pl->segs.size() + pl->ssegs.size()))) != MCD_OK)
+        return st;
+    if ((st = plan_alloc(pl, &pl->d_stiles, stiles.size())) != MCD_OK) return st;
+    if ((st = plan_alloc(pl, &pl->d_slist, slist.size())) != MCD_OK) return st;
     if (grad_kernel && (st = plan_alloc(pl, &pl->d_gacc, pl->gacc_len)) != MCD_OK) return st;
 
     if ((st = plan_upload(pl, pl->d_designs, designs)) != MCD_OK) return st;
@@ -367,6 +490,8 @@ mcd_status plan_build(mcd_ctx* ctx, const mcd_problem* pr, int32_t flags, int32_
     if ((st = plan_upload(pl, pl->d_L_off, L_off)) != MCD_OK) return st;
     if ((st = plan_upload(pl, pl->d_n_draws, n_draws)) != MCD_OK) return st;
     if ((st = plan_upload(pl, pl->d_batch_draws, batch_draws)) != MCD_OK) return st;
+    if ((st = plan_upload(pl, pl->d_stiles, stiles)) != MCD_OK) return st;
+    if ((st = plan_upload(pl, pl->d_slist, slist)) != MCD_OK) return st;
 
     if (flags & MCD_PLAN_TIMING) {
         for (int i = 0; i < 2; ++i) {
@@ -413,7 +538,8 @@ mcd_status enqueue(mcd_plan* pl, const LaunchArgs& a, cudaStream_t stream) {
     if (a.grad && (pl->k > 0) != (a.jac != nullptr))
         return fail(ctx, MCD_EINVAL, "the Jacobian must be given exactly when the plan has k > 0");
     if (a.grad && !pl->d_gacc && pl->gacc_len) return fail(ctx, MCD_EINVAL, "plan has no gradient workspace");
-    MCD_CUDA(cudaMemsetAsync(pl->d_ticket, 0, sizeof(unsigned int) * std::max<size_t>(1, pl->segs.size()), stream),
+    MCD_CUDA(cudaMemsetAsync(pl->d_ticket, 0,
+                             sizeof(unsigned int) * std::max<size_t>(1, pl->segs.size() + pl->ssegs.size()), stream),
              "memset");
     if (pl->J > 0) MCD_CUDA(cudaMemsetAsync(pl->d_hits, 0, sizeof(unsigned long long) * pl->J, stream), "memset");
     if (a.grad && pl->gacc_len)
@@ -426,15 +552,9 @@ mcd_status enqueue(mcd_plan* pl, const LaunchArgs& a, cudaStream_t stream) {
     MCD_CUDA(cudaStreamIsCapturing(stream, &capturing), "cudaStreamIsCapturing");
     const unsigned ev_flags = capturing == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
     if (pl->ev[0]) MCD_CUDA(cudaEventRecordWithFlags(pl->ev[0], stream, ev_flags), "event record");
-    for (size_t q = 0; q < pl->segs.size(); ++q) {
-        const Segment& sg = pl->segs[q];
-        if (sg.n_tiles == 0) continue;
-        SampleParams sp;
+    auto base_params = [&](SampleParams& sp) {
         std::memset(&sp, 0, sizeof(sp));
         sp.designs = pl->d_designs;
-        sp.tiles = pl->d_tiles + sg.tile_begin;
-        sp.n_tiles = sg.n_tiles;
-        sp.ticket = pl->d_ticket + q;
         sp.L32 = pl->d_L32;
         sp.L64 = pl->d_L64;
         sp.L_off = pl->d_L_off;
@@ -448,6 +568,25 @@ mcd_status enqueue(mcd_plan* pl, const LaunchArgs& a, cudaStream_t stream) {
         sp.hinv = (a.grad && a.h > 0.0) ? 1.0 / a.h : 0.0;
         sp.status = ctx->d_status;
         fill_round_keys(a.seed, sp);
+    };
+    for (size_t q = 0; q < pl->ssegs.size(); ++q) {
+        const SharedSeg& sg = pl->ssegs[q];
+        if (sg.n_tiles == 0) continue;
+        SampleParams sp;
+        base_params(sp);
+        sp.n_tiles = sg.n_tiles;
+        sp.ticket = pl->d_ticket + pl->segs.size() + q;
+        MCD_CUDA(launch_shared(sg.d, a.grad, sp, pl->d_stiles + sg.tile_begin, pl->d_slist, sg.grid, stream),
+                 "shared-draw launch");
+    }
+    for (size_t q = 0; q < pl->segs.size(); ++q) {
+        const Segment& sg = pl->segs[q];
+        if (sg.n_tiles == 0) continue;
+        SampleParams sp;
+        base_params(sp);
+        sp.tiles = pl->d_tiles + sg.tile_begin;
+        sp.n_tiles = sg.n_tiles;
+        sp.ticket = pl->d_ticket + q;
         MCD_CUDA(launch_sample(sg.d_lo, sg.d_hi, a.grad, pl->fp64, sp, sg.grid, sg.cfg.threads, stream),
                  "sampling launch");
     }
@@ -564,7 +703,8 @@ mcd_status autotune(mcd_ctx* ctx, const mcd_problem* pr, int32_t flags, int32_t 
                 mcd_plan trial;
                 // timing plans take no Jacobian (k = 0): the finalisation is
                 // the same per-design work either way
-                st = plan_build(ctx, pr, flags & ~(MCD_PLAN_GRAPH | MCD_PLAN_TIMING), 0, &trial, filt);
+                st = plan_build(ctx, pr, flags & ~(MCD_PLAN_GRAPH | MCD_PLAN_TIMING | MCD_PLAN_SHARED), 0, &trial,
+                                filt);
                 LaunchArgs la;
                 la.grad = grad;
                 la.h = grad ? 0.01 : 0.0;
@@ -654,7 +794,8 @@ mcd_status mcd_sync_status(mcd_ctx* ctx, mcd_stream stream) {
 mcd_status mcd_plan_create(mcd_ctx* ctx, const mcd_problem* prob, int32_t flags, int32_t k, mcd_plan** plan) {
     if (!ctx || !plan) return fail(ctx, MCD_EINVAL, "ctx and plan must not be NULL");
     *plan = nullptr;
-    if (flags & ~(MCD_PLAN_GRAD | MCD_PLAN_AUTOTUNE | MCD_PLAN_GRAPH | MCD_PLAN_FP64 | MCD_PLAN_TIMING))
+    if (flags & ~(MCD_PLAN_GRAD | MCD_PLAN_AUTOTUNE | MCD_PLAN_GRAPH | MCD_PLAN_FP64 | MCD_PLAN_TIMING |
+                  MCD_PLAN_SHARED))
         return fail(ctx, MCD_EINVAL, "unknown plan flags");
     mcd_status st = validate_problem(ctx, prob, k);
     if (st != MCD_OK) return st;
@@ -720,7 +861,17 @@ mcd_status mcd_plan_grad(mcd_plan* plan, uint64_t seed, const double* dt_dtheta,
 
 mcd_status mcd_plan_config(const mcd_plan* plan, int32_t d, int32_t* threads, int64_t* tile_draws,
                            int32_t* blocks_per_sm) {
-    if (!plan || d < 1 || d > MCD_MAX_D || plan->seg_of_d[d] < 0) return MCD_EINVAL;
+    if (!plan || d < 1 || d > MCD_MAX_D) return MCD_EINVAL;
+    if (plan->seg_of_d[d] < 0) {
+        for (const SharedSeg& sg : plan->ssegs) {
+            if (sg.d != d) continue;
+            if (threads) *threads = kSharedThreads;
+            if (tile_draws) *tile_draws = sg.tile_draws;
+            if (blocks_per_sm) *blocks_per_sm = sg.blocks_per_sm;
+            return MCD_OK;
+        }
+        return MCD_EINVAL;
+    }
     const Segment& sg = plan->segs[plan->seg_of_d[d]];
     if (threads) *threads = sg.cfg.threads;
     if (tile_draws) *tile_draws = plan->tile_draws_of_d[d];
@@ -728,7 +879,7 @@ mcd_status mcd_plan_config(const mcd_plan* plan, int32_t d, int32_t* threads, in
     return MCD_OK;
 }
 
-int64_t mcd_plan_tiles(const mcd_plan* plan) { return plan ? plan->n_tiles : -1; }
+int64_t mcd_plan_tiles(const mcd_plan* plan) { return plan ? plan->n_tiles + plan->n_shared_tiles : -1; }
 
 mcd_status mcd_plan_kernel_ms(mcd_plan* plan, float* ms) {
     if (!plan || !ms) return MCD_EINVAL;

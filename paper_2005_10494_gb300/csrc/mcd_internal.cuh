@@ -38,6 +38,20 @@ struct TileRec {
     uint32_t pad;
 };
 
+// One unit of work of the shared-draw kernel: draws [start, start + n) of
+// one stream, tested against the designs list[list_off .. list_off + list_cnt).
+struct SharedTile {
+    uint64_t start;      // absolute draw index
+    uint64_t key;        // stream key common to the listed designs
+    uint32_t n;          // draws in the tile
+    uint32_t list_off;
+    uint32_t list_cnt;   // designs in the tile (<= kSharedThreads * designs per thread)
+    uint32_t batch;      // batch-means slot of this draw range
+    int32_t  scen;
+    int32_t  pad;
+};
+constexpr int kSharedThreads = 256;    // block size of the shared-draw kernel
+
 // Device status word: code and index of the first error.
 struct DevStatus {
     int32_t code;
@@ -72,6 +86,13 @@ cudaError_t launch_sample(int d_lo, int d_hi, bool grad, bool fp64, const Sample
                           int grid, int threads, cudaStream_t stream);
 int  sample_kernel_regs(int d_lo, int d_hi, bool grad, bool fp64);
 cudaError_t sample_occupancy(int d_lo, int d_hi, bool grad, bool fp64, int threads, int* blocks);
+
+// Shared-draw kernel of dimension d (FP32 only).
+cudaError_t launch_shared(int d, bool grad, const SampleParams& p, const SharedTile* tiles, const uint32_t* list,
+                          int grid, cudaStream_t stream);
+cudaError_t shared_occupancy(int d, bool grad, int* blocks);
+int shared_designs_per_thread(int d, bool grad);
+int shared_batch_draws(int d);
 
 cudaError_t launch_cholesky(const double* Sigma, const int64_t* sig_off, const int32_t* scen_d,
                             const int64_t* L_off, int n_scen, float* L32, double* L64,

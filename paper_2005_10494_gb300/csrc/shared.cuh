@@ -1,0 +1,239 @@
+// Shared-draw sampling: designs with the same scenario, stream key and draw
+// range see identical draws (common random numbers), so the draws need to be
+// made only once for all of them.
+//
+// A tile is (chunk of up to 256 * kDpt designs of one sharing group, draw
+// range).  For each batch of draws the block makes the normals and y = L z
+// once, with the per-design kernel's Philox / Box-Muller / transform
+// arithmetic, into shared memory; then every thread tests its designs against
+// every draw of the batch (broadcast shared loads).  A design's indicator is
+// the same FP32 comparison as in the per-design kernel, so hit counts are
+// bit-identical to it; the gradient sums differ only in the order of FP32
+// additions.  Draws outside the tile's range enter as y = -inf, z = 0, which
+// no region test counts and which add nothing to any sum.
+//
+// The paper's two-layer estimator (Sec. 2.2, Eq. 7) has this form too: its
+// outer prior samples act as designs (thresholds b - S Delta_k) that share
+// one inner stream of draws.
+#pragma once
+
+#include <cstdint>
+
+#include "mcd_internal.cuh"
+#include "rng.cuh"
+#include "sample.cuh"
+
+namespace mcd {
+
+template <int D, bool GRAD>
+struct SharedShape {
+    static constexpr int kDP = (D + 3) / 4 * 4;                      // padded coordinates per draw
+    // designs per thread: enough to amortise the shared loads, few enough to
+    // keep t (and the gradient sums) in registers
+    static constexpr int kDpt = GRAD ? (D <= 4 ? 4 : (D <= 8 ? 2 : 1)) : (D <= 10 ? 4 : 2);
+    static constexpr int kBD = kSharedThreads * Shape<D>::kG;        // draws per batch (one group per thread)
+    static constexpr size_t kSmem = static_cast<size_t>(kBD) * kDP * sizeof(float) * (GRAD ? 2 : 1);
+};
+
+// The batch's draws: this thread makes group `gi` (kG draws) and writes y
+// (and z for the adjoint) to shared memory; `bsum` gathers z of the valid
+// draws.
+template <int D, bool GRAD>
+__device__ __forceinline__ void make_batch(const float* __restrict__ sL, uint64_t call, uint32_t call_lo,
+                                           bool fast, const Round1& r1, uint64_t key, const SampleParams& P,
+                                           uint32_t base, uint32_t ofs, uint32_t n, float* sy, float* sz,
+                                           float* bsum) {
+    using S = Shape<D>;
+    constexpr int DP = SharedShape<D, GRAD>::kDP;
+    float z[S::kNZ];
+#pragma unroll
+    for (int c = 0; c < S::kNC; ++c) {
+        uint4 w;
+        if (fast) w = philox_fast(call_lo + c, r1, P.rk0, P.rk1);
+        else w = philox_full(call + c, key, P.rk0, P.rk1);
+        normals4<float>(w, &z[4 * c]);
+    }
+#pragma unroll
+    for (int g = 0; g < S::kG; ++g) {
+        const bool valid = (base + g - ofs) < n;
+        float y[DP], zz[DP];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const int row = LPad<float>::rowoff(i);
+            float s = sL[row] * z[g * D];
+#pragma unroll
+            for (int j = 1; j <= i; ++j) s = fmadd(sL[row + j], z[g * D + j], s);
+            y[i] = valid ? s : -INFINITY;
+            zz[i] = valid ? z[g * D + i] : 0.0f;
+            if constexpr (GRAD) bsum[i] += zz[i];
+        }
+#pragma unroll
+        for (int i = D; i < DP; ++i) { y[i] = -INFINITY; zz[i] = 0.0f; }
+        float4* yv = reinterpret_cast<float4*>(sy + (threadIdx.x * S::kG + g) * DP);
+#pragma unroll
+        for (int v = 0; v < DP / 4; ++v) yv[v] = make_float4(y[4 * v], y[4 * v + 1], y[4 * v + 2], y[4 * v + 3]);
+        if constexpr (GRAD) {
+            float4* zv = reinterpret_cast<float4*>(sz + (threadIdx.x * S::kG + g) * DP);
+#pragma unroll
+            for (int v = 0; v < DP / 4; ++v) zv[v] = make_float4(zz[4 * v], zz[4 * v + 1], zz[4 * v + 2], zz[4 * v + 3]);
+        }
+    }
+}
+
+template <int DP>
+__device__ __forceinline__ void load_row(const float* p, float* v) {
+#pragma unroll
+    for (int q = 0; q < DP / 4; ++q) {
+        const float4 f = reinterpret_cast<const float4*>(p)[q];
+        v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
+    }
+}
+
+template <int D, bool GRAD>
+__global__ void __launch_bounds__(kSharedThreads) shared_kernel(const __grid_constant__ SampleParams P,
+                                                                const SharedTile* __restrict__ tiles,
+                                                                const uint32_t* __restrict__ list) {
+    using S = Shape<D>;
+    using SS = SharedShape<D, GRAD>;
+    constexpr int DPT = SS::kDpt, DP = SS::kDP;
+    extern __shared__ __align__(16) float sh[];
+    float* sy = sh;                                   // [kBD][kDP]
+    float* sz = sh + SS::kBD * DP;                    // [kBD][kDP], adjoint only
+    __shared__ __align__(16) float sL[LPad<float>::rowoff(D) + 4];
+    __shared__ float sB[kMaxWarps][GRAD ? D : 1];
+    __shared__ unsigned int s_tile;
+
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(P.ticket, 1u);
+        __syncthreads();
+        const unsigned int tk = s_tile;
+        if (static_cast<int64_t>(tk) >= P.n_tiles) break;
+        const SharedTile tl = tiles[tk];
+        const int ok = P.scen_ok[tl.scen];
+        const int64_t loff = P.L_off[tl.scen];
+        for (int r = threadIdx.x; r < D; r += blockDim.x) {
+            const int po = LPad<float>::rowoff(r), pk = r * (r + 1) / 2;
+            for (int q = 0; q < LPad<float>::chunks(r) * LPad<float>::V; ++q)
+                sL[po + q] = q <= r ? P.L32[loff + pk + q] : 0.0f;
+        }
+        // this thread's designs (list positions threadIdx.x + q * blockDim.x)
+        // and their thresholds; a missing design gets t = +inf (never a hit)
+        const int nq = static_cast<int>((tl.list_cnt + blockDim.x - 1) / blockDim.x);   // block-uniform
+        int dsg[DPT];
+        float t[DPT][D], tsc[DPT][GRAD ? D : 1];
+#pragma unroll
+        for (int q = 0; q < DPT; ++q) {
+            const uint32_t li = threadIdx.x + q * blockDim.x;
+            dsg[q] = li < tl.list_cnt ? static_cast<int>(list[tl.list_off + li]) : -1;
+            const int64_t vo = dsg[q] >= 0 ? P.designs[dsg[q]].vec_off : 0;
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                const double tt = dsg[q] >= 0 ? P.b[vo + i] - P.mu[vo + i] : 0.0;
+                if (dsg[q] >= 0 && tt != tt) set_status(P.status, MCD_ENAN, dsg[q]);
+                t[q][i] = dsg[q] >= 0 ? static_cast<float>(tt) : INFINITY;
+                if constexpr (GRAD)
+                    tsc[q][i] = (P.hinv_log2e != 0.0f && dsg[q] >= 0) ? static_cast<float>(tt) * P.hinv_log2e : 0.0f;
+            }
+        }
+        __syncthreads();                              // sL complete
+        if (!ok) continue;                            // block-uniform; the next ticket read is behind a barrier
+
+        const uint64_t g_first = tl.start / S::kG;
+        const uint32_t ofs = static_cast<uint32_t>(tl.start - g_first * S::kG);
+        const uint32_t ngroups = (ofs + tl.n + S::kG - 1) / S::kG;
+        const uint64_t call_first = g_first * static_cast<uint64_t>(S::kNC);
+        const uint64_t call_last = (g_first + ngroups) * static_cast<uint64_t>(S::kNC) - 1;
+        const bool fast = (call_first >> 32) == (call_last >> 32);
+        const Round1 r1 = round1_consts(static_cast<uint32_t>(call_first >> 32), tl.key, P.rk0, P.rk1);
+
+        uint32_t cnt[DPT];
+        float A[DPT][GRAD ? D : 1], G[DPT][GRAD ? D : 1], bsum[GRAD ? D : 1];
+#pragma unroll
+        for (int q = 0; q < DPT; ++q) {
+            cnt[q] = 0;
+#pragma unroll
+            for (int i = 0; i < (GRAD ? D : 1); ++i) { A[q][i] = 0.0f; G[q][i] = 0.0f; }
+        }
+#pragma unroll
+        for (int i = 0; i < (GRAD ? D : 1); ++i) bsum[i] = 0.0f;
+        const float hl2e = GRAD ? P.hinv_log2e : 0.0f;
+
+        for (uint32_t g0 = 0; g0 < ngroups; g0 += blockDim.x) {
+            const uint32_t gi = g0 + threadIdx.x;
+            make_batch<D, GRAD>(sL, call_first + static_cast<uint64_t>(gi) * S::kNC,
+                                static_cast<uint32_t>(call_first) + gi * S::kNC, fast, r1, tl.key, P,
+                                gi * S::kG, ofs, gi < ngroups ? tl.n : 0u, sy, sz, bsum);
+            __syncthreads();
+            const int nb = static_cast<int>(min(static_cast<uint32_t>(SS::kBD), (ngroups - g0) * S::kG));
+            for (int dn = 0; dn < nb; ++dn) {
+                float y[DP];
+                load_row<DP>(sy + dn * DP, y);
+                float zz[GRAD ? DP : 4];
+                if constexpr (GRAD) load_row<DP>(sz + dn * DP, zz);
+#pragma unroll
+                for (int q = 0; q < DPT; ++q) {
+                    if (q >= nq) break;
+                    bool hit = false;
+#pragma unroll
+                    for (int i = 0; i < D; ++i) hit |= (y[i] > t[q][i]);
+                    cnt[q] += hit ? 1u : 0u;
+                    if constexpr (GRAD) {
+                        const float hv = hit ? 1.0f : 0.0f;
+#pragma unroll
+                        for (int i = 0; i < D; ++i) A[q][i] = fmadd(hv, zz[i], A[q][i]);
+                        if (hl2e != 0.0f) {
+                            float keep[D], prod = 1.0f;
+#pragma unroll
+                            for (int i = 0; i < D; ++i) {
+                                keep[i] = smooth_keep(y[i], t[q][i], tsc[q][i], hl2e, 0.0);
+                                prod *= keep[i];
+                            }
+#pragma unroll
+                            for (int i = 0; i < D; ++i) G[q][i] = fmadd(prod, 1.0f - keep[i], G[q][i]);
+                        }
+                    }
+                }
+            }
+            __syncthreads();                          // the next batch rewrites sy / sz
+        }
+
+        // hits: each design of the tile belongs to exactly one thread
+#pragma unroll
+        for (int q = 0; q < DPT; ++q)
+            if (dsg[q] >= 0 && cnt[q]) atomicAdd(&P.hits[dsg[q]], static_cast<unsigned long long>(cnt[q]));
+        if constexpr (GRAD) {
+            // the sum of z over the tile's draws is common to all its designs
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                const float w = warp_sum(bsum[i]);
+                if (lane == 0) sB[warp][i] = w;
+            }
+            __syncthreads();
+            const double fix = static_cast<double>(1ull << kGradFixBits);
+#pragma unroll
+            for (int q = 0; q < DPT; ++q) {
+                if (dsg[q] < 0) continue;
+                unsigned long long* slot = P.gacc + P.designs[dsg[q]].acc_off + static_cast<int64_t>(tl.batch) * 3 * D;
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    double s = 0.0;
+                    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) s += static_cast<double>(sB[w][i]);
+                    atomicAdd(slot + i, static_cast<unsigned long long>(__double2ll_rn(static_cast<double>(A[q][i]) * fix)));
+                    atomicAdd(slot + D + i, static_cast<unsigned long long>(__double2ll_rn(s * fix)));
+                    atomicAdd(slot + 2 * D + i, static_cast<unsigned long long>(__double2ll_rn(static_cast<double>(G[q][i]) * fix)));
+                }
+            }
+        }
+        // the next iteration's ticket read sits behind a barrier, so sB and
+        // the per-tile shared state are not overwritten early
+    }
+}
+
+template <int D, bool GRAD>
+const void* shared_fn() { return reinterpret_cast<const void*>(&shared_kernel<D, GRAD>); }
+
+template <int D, bool GRAD>
+size_t shared_smem() { return SharedShape<D, GRAD>::kSmem; }
+
+}  // namespace mcd

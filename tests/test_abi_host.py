@@ -78,3 +78,15 @@ def test_oracle_is_independent_of_the_cuda_path():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in text.replace("oracle's", ""), f
+
+
+def test_binding_constants_match_the_header():
+    import paper_2005_10494_gb300.binding as b
+    text = open(HEADER).read()
+    defs = dict(re.findall(r"^#define\s+(MCD_\w+)\s+(-?\d+)", text, re.M))
+    for name, val in defs.items():
+        if hasattr(b, name):
+            assert getattr(b, name) == int(val), name
+    for name in ["MCD_PLAN_GRAD", "MCD_PLAN_AUTOTUNE", "MCD_PLAN_GRAPH", "MCD_PLAN_FP64", "MCD_PLAN_TIMING",
+                 "MCD_PLAN_SHARED", "MCD_SHARED_MIN", "MCD_MAX_D", "MCD_ANY_EXCEEDS", "MCD_ALL_BELOW"]:
+        assert name in defs and hasattr(b, name), name

@@ -405,3 +405,31 @@ def random_problem(rng, n_scen=3, designs_per=(1, 6), d_choices=(1, 2, 3, 4, 5, 
     begin = rng.integers(0, 1000, size=J)
     return Problem("random", sigmas, scen, mus, bs, nd, keys, draw_begin=begin,
                    structures=[{"kind": "dense"}] * n_scen)
+
+
+def crn_groups(rng, d_list=(1, 3, 5, 8, 10, 13, 20), group=40, extra=3, n_draws=20_011, draw_begin=7,
+               big_group_d=None, big_group=0):
+    """Common-random-number groups for the shared-draw path: per dimension one
+    LKJ(2) scenario with `group` designs sharing stream key, first draw and
+    draw count, plus `extra` designs of their own keys; optionally one more
+    group of `big_group` designs at dimension `big_group_d` (several chunks)."""
+    sigmas, mus, bs, scen, nd, keys, begin = [], [], [], [], [], [], []
+    specs = [(d, group) for d in d_list]
+    if big_group_d is not None and big_group > 0:
+        specs.append((big_group_d, big_group))
+    key = 1000
+    for s, (d, m) in enumerate(specs):
+        sigmas.append(lkj_cvine(d, 2.0, rng) if d > 1 else np.eye(1))
+        for k in range(m + extra):
+            mus.append(rng.normal(0.5, 0.7, size=d))
+            b = rng.normal(1.5, 0.7, size=d)
+            if d > 1 and rng.random() < 0.2:
+                b[int(rng.integers(0, d))] = np.inf
+            bs.append(b)
+            scen.append(s)
+            nd.append(n_draws)
+            begin.append(draw_begin)
+            keys.append(s if k < m else key)
+            key += 1
+    return Problem("crn-groups", sigmas, scen, mus, bs, nd, keys, draw_begin=begin,
+                   structures=[{"kind": "dense"}] * len(sigmas))
