@@ -24,6 +24,10 @@ constexpr int kMaxTaps = (2 * kMaxReach + 1) * (2 * kMaxReach + 1);
 constexpr int kRowsPerBlock = 32;     // output rows of one block (2-D)
 constexpr int kColsPerBlock = 128;    // output columns of one block (2-D)
 constexpr int kLine = 512;            // outputs of one block (1-D)
+// The interior class's FP32 stencil is also stored compactly after the class
+// table, 16-byte aligned, for vector loads (kIntSlot floats, T*T used).
+constexpr int kClassSlots = (kMaxReach + 1) * (kMaxReach + 1) * (kMaxReach + 1) * (kMaxReach + 1);
+constexpr int kIntSlot = 64;
 
 __host__ __device__ inline int reach_of(double bw) {
     const double f = floor(bw);
@@ -60,7 +64,13 @@ __global__ void weights_kernel(int R, double bw, int degree, bool two_d, int gx,
     const int T = 2 * R + 1;
     double* w = w64 + static_cast<int64_t>(id) * kMaxTaps;
     float* wf = w32 + static_cast<int64_t>(id) * kMaxTaps;
+    // the thread of the interior class pair also fills the compact copy
+    // (zeros when this grid has no interior point)
+    float* wint = (xlo == R && xhi == R && (!two_d || (ylo == R && yhi == R)))
+                      ? w32 + static_cast<int64_t>(kClassSlots) * kMaxTaps : nullptr;
     for (int q = 0; q < kMaxTaps; ++q) { w[q] = 0.0; wf[q] = 0.0f; }
+    if (wint)
+        for (int q = 0; q < kIntSlot; ++q) wint[q] = 0.0f;
     // classes that no position of this grid has are skipped
     if (xlo + xhi + 1 > gx || (xlo < R && xhi < R && xlo + xhi + 1 != gx)) return;
     if (two_d && (ylo + yhi + 1 > gy || (ylo < R && yhi < R && ylo + yhi + 1 != gy))) return;
@@ -103,6 +113,7 @@ __global__ void weights_kernel(int R, double bw, int degree, bool two_d, int gx,
             const int q = two_d ? (dx + R) * T + (dy + R) : (dx + R);
             w[q] = W * s;
             wf[q] = static_cast<float>(W * s);
+            if (wint) wint[q] = wf[q];
         }
     }
 }
@@ -201,26 +212,144 @@ struct RunMax {
     }
 };
 
-// 2-D stencil: block = kRowsPerBlock x kColsPerBlock outputs of one scenario.
-// Staging: warp w copies tile rows w, w+8, ... (lanes along the row, the
-// column bounds fixed per lane), converting FP64 to FP32.  Compute: thread
-// (tx, ty) owns the 4 x 4 outputs at rows 4 ty.., columns 4 tx..; when all of
-// them are interior (R points on every side) it streams the 4 + 2R input rows
-// of its window through registers with 16-byte shared loads and applies the
-// interior stencil (in registers); edge threads use each point's edge-class
-// stencil with scalar loads.
-template <int R, bool RAW>
-__global__ void __launch_bounds__(256) smooth2d_kernel(const unsigned long long* __restrict__ val, int g1, int g2,
-                                                       const float* __restrict__ w32,
+// Fast FP64 -> FP32 for exponents 897..1150 (the FP32 normal range): one
+// funnel shift moves exponent and mantissa together, one subtraction
+// rebiases, the sign is or-ed back; the result truncates like d2f_bits.
+// `bad` collects values outside that range, which the caller converts again
+// with d2f_bits.
+__device__ __forceinline__ float d2f_fast(unsigned long long b, bool& bad) {
+    const unsigned hi = static_cast<unsigned>(b >> 32), lo = static_cast<unsigned>(b);
+    bad |= ((hi & 0x7fffffffu) - 0x38100000u) >= 0x0fe00000u;
+    const unsigned mag = __funnelshift_l(lo, hi, 3) - (896u << 23);
+    return __uint_as_float((hi & 0x80000000u) | mag);
+}
+
+// Fast FP32 -> FP64 bits for normal, finite f (same result as f2d_bits):
+// hi = (u >> 3) + 896 << 20 moves and rebiases the exponent, and for
+// negative f the sign bit shifted to bit 28 is moved back to bit 31 by adding
+// 0x70000000.  `bad` collects zeros, subnormals, infinities and NaNs.
+__device__ __forceinline__ unsigned long long f2d_fast(float f, bool& bad) {
+    const unsigned u = __float_as_uint(f);
+    bad |= !(fabsf(f) >= 0x1p-126f && fabsf(f) <= 0x1.fffffep127f);
+    const unsigned hi = (u >> 3) + 0x38000000u + ((u >> 31) ? 0x70000000u : 0u);
+    return (static_cast<unsigned long long>(hi) << 32) | (u << 29);
+}
+
+// Store the pair (x0, x1) of staged row rr, pair slot m, at shared columns
+// 2m - E + R and 2m - E + R + 1 (column -1 of odd R is not needed).
+template <int R, int E, int NPR, int SR, int SCP>
+__device__ __forceinline__ void store_pair(float (*tile)[SCP], int rr, int m, float x0, float x1) {
+    if (rr >= SR || m >= NPR) return;
+    const int sc = 2 * m - E + R;
+    if constexpr (R % 2 == 0) {
+        *reinterpret_cast<float2*>(&tile[rr][sc]) = make_float2(x0, x1);
+    } else {
+        if (sc >= 0) tile[rr][sc] = x0;
+        tile[rr][sc + 1] = x1;
+    }
+}
+
+// Staging of tile rows warp + 8 k, k in [K0, K1), into FP32 shared memory.
+// Input column c0 - R sits at shared column 0.  Lane l takes the pairs of
+// doubles l, l + 32, l + 64 of a row, pair m covering global columns
+// c0 - E + 2m and c0 - E + 2m + 1 (E = R rounded up to even, so that with VEC
+// every pair is one aligned 16-byte load).  All loads of the batch are issued
+// before any value is converted.  Positions outside the grid hold 1.0: their
+// weight in every stencil that reads them is zero, and a finite value keeps
+// 0 * x = 0.
+template <int R, bool RAW, bool VEC, int K0, int K1, int SR, int SCP>
+__device__ __forceinline__ void stage_rows(const unsigned long long* __restrict__ V, int g1, int g2, int r0, int c0,
+                                           float (*tile)[SCP], RunMax& raw) {
+    constexpr int E = (R + 1) / 2 * 2;
+    constexpr int NPR = (kColsPerBlock + 2 * E) / 2;        // pairs per staged row
+    constexpr int PPL = (NPR + 31) / 32;                    // pair slots per lane
+    constexpr int NK = K1 - K0;
+    constexpr unsigned long long kOne = 0x3ff0000000000000ull;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned long long b0[NK][PPL], b1[NK][PPL];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        const int rr = warp + 8 * (K0 + k);
+        const int gr = r0 - R + rr;
+        const bool row_in = rr < SR && gr >= 0 && gr < g1;
+#pragma unroll
+        for (int p = 0; p < PPL; ++p) {
+            const int m = lane + 32 * p;
+            const int gc = c0 - E + 2 * m;
+            b0[k][p] = kOne;
+            b1[k][p] = kOne;
+            if (row_in && m < NPR) {
+                const unsigned long long* q = V + static_cast<int64_t>(gr) * g2 + gc;
+                if constexpr (VEC) {
+                    if (gc >= 0 && gc < g2) {
+                        const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(q));
+                        b0[k][p] = v.x;
+                        b1[k][p] = v.y;
+                    }
+                } else {
+                    if (gc >= 0 && gc < g2) b0[k][p] = __ldg(q);
+                    if (gc + 1 >= 0 && gc + 1 < g2) b1[k][p] = __ldg(q + 1);
+                }
+            }
+        }
+    }
+    // fast conversions go straight to shared memory; in the rare batch that
+    // holds a value outside the fast range the warp converts and stores
+    // every value again with the exact routine
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        const int rr = warp + 8 * (K0 + k);
+#pragma unroll
+        for (int p = 0; p < PPL; ++p) {
+            const float x0 = d2f_fast(b0[k][p], bad), x1 = d2f_fast(b1[k][p], bad);
+            store_pair<R, E, NPR, SR, SCP>(tile, rr, lane + 32 * p, x0, x1);
+        }
+    }
+    const bool slow = __any_sync(0xffffffffu, bad);
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        const int rr = warp + 8 * (K0 + k);
+#pragma unroll
+        for (int p = 0; p < PPL; ++p) {
+            const int m = lane + 32 * p;
+            float x0 = 0.0f, x1 = 0.0f;
+            if (slow || RAW) { x0 = d2f_bits(b0[k][p]); x1 = d2f_bits(b1[k][p]); }
+            if (slow) store_pair<R, E, NPR, SR, SCP>(tile, rr, m, x0, x1);
+            if constexpr (RAW) {
+                const int gr = r0 - R + rr, gc = c0 - E + 2 * m;
+                if (rr < SR && m < NPR && rr >= R && rr < R + kRowsPerBlock && gr < g1) {
+                    if (gc >= c0 && gc < c0 + kColsPerBlock && gc < g2)
+                        raw.add(x0, b0[k][p], static_cast<long long>(gr) * g2 + gc);
+                    if (gc + 1 >= c0 && gc + 1 < c0 + kColsPerBlock && gc + 1 < g2)
+                        raw.add(x1, b1[k][p], static_cast<long long>(gr) * g2 + gc + 1);
+                }
+            }
+        }
+    }
+}
+
+// 2-D stencil: one block = kRowsPerBlock x kColsPerBlock outputs of one
+// scenario, 256 threads.  The input window is staged as FP32 (stage_rows, in
+// three batches of rows, each with all its loads in flight at once).  Thread
+// (tx, ty) owns the 4 x 4 outputs at rows 4 ty.., columns 4 tx..; it applies
+// the interior stencil to all of them, streaming the 4 + 2R rows of its
+// window through registers with 16-byte shared loads, and keeps the outputs
+// whose edge class is interior.  The block's edge outputs (fewer than R
+// points to a grid edge) follow, one per thread, with their class stencils.
+// VEC: g2 even and the input 16-byte aligned (pairs of doubles per load).
+template <int R, bool RAW, bool VEC>
+__global__ void __launch_bounds__(256, 4) smooth2d_kernel(const unsigned long long* __restrict__ val, int g1, int g2,
+                                                       const float* __restrict__ w32, const float* __restrict__ wint,
                                                        unsigned long long* __restrict__ out,
                                                        unsigned long long* part_v, long long* part_i,
                                                        unsigned long long* rpart_v, long long* rpart_i) {
     constexpr int T = 2 * R + 1;
-    constexpr int SR = kRowsPerBlock + 2 * R, SC = kColsPerBlock + 2 * R;
-    constexpr int SCP = (SC + 3) / 4 * 4;                   // row stride: whole 16-byte vectors
-    constexpr int CPL = (SC + 31) / 32;                     // row chunks per lane
+    constexpr int SR = kRowsPerBlock + 2 * R;               // staged rows
     constexpr int NIC = 4 + 2 * R;                          // input columns of a thread's window
     constexpr int NV = (NIC + 3) / 4;                       // 16-byte loads per window row
+    constexpr int SCP = 4 * 31 + 4 * NV;                    // shared row stride (floats)
+    constexpr int RPW = (SR + 7) / 8;                       // staged rows per warp
     __shared__ __align__(16) float tile[SR][SCP];
     __shared__ unsigned long long sv[8];
     __shared__ long long si[8];
@@ -229,52 +358,31 @@ __global__ void __launch_bounds__(256) smooth2d_kernel(const unsigned long long*
     const int s = blockIdx.z;
     const int r0 = blockIdx.y * kRowsPerBlock, c0 = blockIdx.x * kColsPerBlock;
     const unsigned long long* V = val + static_cast<int64_t>(s) * g1 * g2;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     RunMax raw;
     raw.init();
-    bool col_in[CPL], col_own[CPL];
-#pragma unroll
-    for (int k = 0; k < CPL; ++k) {
-        const int cc = lane + 32 * k, gc = c0 - R + cc;
-        col_in[k] = cc < SC && gc >= 0 && gc < g2;
-        col_own[k] = cc >= R && cc < R + kColsPerBlock;
-    }
-    for (int rr = warp; rr < SR; rr += 8) {
-        const int gr = r0 - R + rr;
-        const bool row_in = gr >= 0 && gr < g1;
-        const bool row_own = rr >= R && rr < R + kRowsPerBlock;
-        const unsigned long long* rowp = V + static_cast<int64_t>(gr) * g2 + (c0 - R + lane);
-        unsigned long long bits[CPL];
-#pragma unroll
-        for (int k = 0; k < CPL; ++k) bits[k] = (row_in && col_in[k]) ? __ldg(rowp + 32 * k) : 0ull;
-#pragma unroll
-        for (int k = 0; k < CPL; ++k) {
-            const int cc = lane + 32 * k;
-            if (cc < SCP) {
-                const bool in = row_in && col_in[k];
-                const float x = in ? d2f_bits(bits[k]) : 0.0f;
-                if (RAW && in && row_own && col_own[k])
-                    raw.add(x, bits[k], static_cast<long long>(gr) * g2 + (c0 - R + cc));
-                tile[rr][cc] = x;
-            }
-        }
-    }
+    static_assert(RPW == 5, "staging batches assume 5 rows per warp");
+    stage_rows<R, RAW, VEC, 0, 2, SR, SCP>(V, g1, g2, r0, c0, tile, raw);
+    stage_rows<R, RAW, VEC, 2, 4, SR, SCP>(V, g1, g2, r0, c0, tile, raw);
+    stage_rows<R, RAW, VEC, 4, 5, SR, SCP>(V, g1, g2, r0, c0, tile, raw);
     __syncthreads();
+
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int orow = r0 + 4 * ty, ocol = c0 + 4 * tx;       // first output of this thread
-    float best = -INFINITY;
-    long long best_i = -1;
     const int ncls = (R + 1) * (R + 1);
-    const int interior = R * (R + 1) + R;                  // class with R points on both sides
     unsigned long long* O = out ? out + static_cast<int64_t>(s) * g1 * g2 : nullptr;
-    // Phase A, no divergence: every thread applies the interior stencil to its
-    // whole 4 x 4 patch and keeps the outputs whose edge class is interior.
-    float keep[4][4];
+    float best = -INFINITY;
+    // Interior stencil of every output of the patch.  The interior window is
+    // symmetric (tricube product weights, monomial basis), so its stencil
+    // depends only on (|u|, |v|) sorted: (R+1)(R+2)/2 distinct weights, read
+    // at the canonical positions (R + a, R + b), a <= b.
+    float acc[4][4];
     {
-        float wi[T * T];                                   // interior stencil, in registers
+        constexpr int NC = (R + 1) * (R + 2) / 2;
+        float wc[NC];
 #pragma unroll
-        for (int q = 0; q < T * T; ++q) wi[q] = __ldg(&w32[static_cast<int64_t>(interior * ncls + interior) * kMaxTaps + q]);
-        float acc[4][4];
+        for (int a = 0, n = 0; a <= R; ++a)
+#pragma unroll
+            for (int b = a; b <= R; ++b, ++n) wc[n] = __ldg(&wint[(R + a) * T + (R + b)]);
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -295,24 +403,36 @@ __global__ void __launch_bounds__(256) smooth2d_kernel(const unsigned long long*
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
 #pragma unroll
-                    for (int dy = 0; dy < T; ++dy) acc[i][j] = fmaf(wi[dx * T + dy], in[j + dy], acc[i][j]);
+                    for (int dy = 0; dy < T; ++dy) {
+                        const int u = dx < R ? R - dx : dx - R, v = dy < R ? R - dy : dy - R;
+                        const int a = u < v ? u : v, b = u < v ? v : u;
+                        // canonical index of (a, b): rows a' < a hold R + 1 - a' entries
+                        const int n = a * (R + 1) - a * (a - 1) / 2 + (b - a);
+                        acc[i][j] = fmaf(wc[n], in[j + dy], acc[i][j]);
+                    }
             }
         }
+    }
+    {
         bool col_int[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) col_int[j] = ocol + j >= R && ocol + j <= g2 - 1 - R;
         const bool all_cols = col_int[0] && col_int[3];
-        // 16-byte stores when the row starts stay 16-byte aligned
-        const bool vec = (g2 % 2) == 0 && (reinterpret_cast<uintptr_t>(O) & 15u) == 0;
+        const bool vec_out = VEC && (reinterpret_cast<uintptr_t>(O) & 15u) == 0;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const bool row_int = orow + i >= R && orow + i <= g1 - 1 - R;
-            const long long idx0 = static_cast<long long>(orow + i) * g2 + ocol;
+            const int64_t idx0 = static_cast<int64_t>(orow + i) * g2 + ocol;
             unsigned long long o[4];
+            bool bad = false;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) o[j] = f2d_bits(acc[i][j]);
+            for (int j = 0; j < 4; ++j) o[j] = f2d_fast(acc[i][j], bad);
+            if (__any_sync(0xffffffffu, bad)) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) o[j] = f2d_bits(acc[i][j]);
+            }
             if (O && row_int) {
-                if (vec && all_cols) {
+                if (vec_out && all_cols) {
                     ulonglong2* dst = reinterpret_cast<ulonglong2*>(O + idx0);
                     dst[0] = make_ulonglong2(o[0], o[1]);
                     dst[1] = make_ulonglong2(o[2], o[3]);
@@ -324,63 +444,50 @@ __global__ void __launch_bounds__(256) smooth2d_kernel(const unsigned long long*
 #pragma unroll
             for (int j = 0; j < 4; ++j) best = fmaxf(best, (row_int && col_int[j]) ? acc[i][j] : -INFINITY);
         }
-        // keep the patch for the index search of the winning threads
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) keep[i][j] = acc[i][j];
     }
-    // Phase B: the block's edge outputs (fewer than R rows or columns to a
-    // grid edge), one per thread, with the stencil of their edge class.
-    // Edge columns (all 32 rows) first, then edge rows (the other columns).
+    // The block's edge outputs (fewer than R rows or columns to a grid edge),
+    // one per thread, with the stencil of their edge class: edge columns (all
+    // rows of the block) first, then edge rows (the other columns).
     float eb_v = -INFINITY;
     long long eb_i = -1;
     {
-        int ecol[2 * R], erow[2 * R];
-        int nec = 0, ner = 0;
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            if (c0 + k < R && c0 + k < g2) ecol[nec++] = c0 + k;                 // left edge
-        }
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            const int c = g2 - R + k;
-            if (c >= R && c >= c0 && c < c0 + kColsPerBlock) ecol[nec++] = c;     // right edge
-        }
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            if (r0 + k < R && r0 + k < g1) erow[ner++] = r0 + k;                 // top edge
-        }
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            const int r = g1 - R + k;
-            if (r >= R && r >= r0 && r < r0 + kRowsPerBlock) erow[ner++] = r;     // bottom edge
-        }
+        const int nl = c0 == 0 ? min(R, g2) : 0;                           // left edge columns 0 .. nl-1
+        const int cr0 = max(max(g2 - R, R), c0), cr1 = min(g2, c0 + kColsPerBlock);
+        const int nr = max(0, cr1 - cr0);                                  // right edge columns cr0 ..
+        const int nt = r0 == 0 ? min(R, g1) : 0;                           // top edge rows 0 .. nt-1
+        const int rb0 = max(max(g1 - R, R), r0), rb1 = min(g1, r0 + kRowsPerBlock);
+        const int nbm = max(0, rb1 - rb0);                                 // bottom edge rows rb0 ..
+        const int nec = nl + nr, ner = nt + nbm;
         const int rows_here = min(kRowsPerBlock, g1 - r0);
         const int n1 = nec * rows_here, n2 = ner * kColsPerBlock;
         for (int t = threadIdx.x; t < n1 + n2; t += blockDim.x) {
             int r, c;
-            if (t < n1) { c = ecol[t / rows_here]; r = r0 + t % rows_here; }
-            else {
-                r = erow[(t - n1) / kColsPerBlock];
+            if (t < n1) {
+                const int e = t / rows_here;
+                c = e < nl ? e : cr0 + (e - nl);
+                r = r0 + t % rows_here;
+            } else {
+                const int e = (t - n1) / kColsPerBlock;
+                r = e < nt ? e : rb0 + (e - nt);
                 c = c0 + (t - n1) % kColsPerBlock;
                 if (c >= g2 || c < R || c > g2 - 1 - R) continue;                // edge columns done above
             }
             const float* w = w32 + static_cast<int64_t>(cls(r, g1, R) * ncls + cls(c, g2, R)) * kMaxTaps;
-            float acc = 0.0f;
+            float a = 0.0f;
 #pragma unroll
             for (int dx = 0; dx < T; ++dx)
 #pragma unroll
                 for (int dy = 0; dy < T; ++dy)
-                    acc = fmaf(__ldg(&w[dx * T + dy]), tile[r - r0 + dx][c - c0 + dy], acc);
+                    a = fmaf(__ldg(&w[dx * T + dy]), tile[r - r0 + dx][c - c0 + dy], a);
             const long long idx = static_cast<long long>(r) * g2 + c;
-            if (O) O[idx] = f2d_bits(acc);
-            if (acc > eb_v || (acc == eb_v && idx < eb_i)) { eb_v = acc; eb_i = idx; }
+            if (O) O[idx] = f2d_bits(a);
+            if (a > eb_v || (a == eb_v && idx < eb_i)) { eb_v = a; eb_i = idx; }
         }
     }
     best = fmaxf(best, eb_v);
     // Argmax: the block's largest value first (max reductions only), then the
     // lowest index holding it, searched by the few threads that hold it.
+    long long best_i;
     {
         float m = best;
 #pragma unroll
@@ -398,7 +505,7 @@ __global__ void __launch_bounds__(256) smooth2d_kernel(const unsigned long long*
                 const bool row_int = orow + i >= R && orow + i <= g1 - 1 - R;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const bool v = row_int && ocol + j >= R && ocol + j <= g2 - 1 - R && keep[i][j] == bm;
+                    const bool v = row_int && ocol + j >= R && ocol + j <= g2 - 1 - R && acc[i][j] == bm;
                     const long long idx = static_cast<long long>(orow + i) * g2 + ocol + j;
                     if (v && (cand < 0 || idx < cand)) cand = idx;
                 }
@@ -511,8 +618,7 @@ int blocks_per_scen(int g1, int g2) {
 }  // namespace
 
 size_t smooth_weight_count() {
-    const int ncls = (kMaxReach + 1) * (kMaxReach + 1);
-    return static_cast<size_t>(ncls) * ncls * kMaxTaps;
+    return static_cast<size_t>(kClassSlots) * kMaxTaps + kIntSlot;
 }
 
 // Per-block argmax candidates: smoothed then raw, n_scen * blocks each.
@@ -545,14 +651,20 @@ cudaError_t smooth_argmax(int n_scen, int g1, int g2, const double* value, doubl
     if (two_d) {
         dim3 grid((g2 + kColsPerBlock - 1) / kColsPerBlock, (g1 + kRowsPerBlock - 1) / kRowsPerBlock, n_scen);
         const bool raw = raw_idx || raw_val;
-        if (raw) {
-            if (R == 1) smooth2d_kernel<1, true><<<grid, 256, 0, stream>>>(vb, g1, g2, wbuf32, ob, pv, pi, rpv, rpi);
-            else if (R == 2) smooth2d_kernel<2, true><<<grid, 256, 0, stream>>>(vb, g1, g2, wbuf32, ob, pv, pi, rpv, rpi);
-            else smooth2d_kernel<3, true><<<grid, 256, 0, stream>>>(vb, g1, g2, wbuf32, ob, pv, pi, rpv, rpi);
-        } else {
-            if (R == 1) smooth2d_kernel<1, false><<<grid, 256, 0, stream>>>(vb, g1, g2, wbuf32, ob, pv, pi, rpv, rpi);
-            else if (R == 2) smooth2d_kernel<2, false><<<grid, 256, 0, stream>>>(vb, g1, g2, wbuf32, ob, pv, pi, rpv, rpi);
-            else smooth2d_kernel<3, false><<<grid, 256, 0, stream>>>(vb, g1, g2, wbuf32, ob, pv, pi, rpv, rpi);
+        // pairs of doubles per load when every row starts on a 16-byte boundary
+        const bool vec = (g2 % 2) == 0 && (reinterpret_cast<uintptr_t>(value) & 15u) == 0;
+        const float* wint = wbuf32 + static_cast<size_t>(kClassSlots) * kMaxTaps;
+        const int key = (R - 1) * 4 + (raw ? 2 : 0) + (vec ? 1 : 0);
+        switch (key) {
+#define MCD_SMOOTH2D(RR, RAW, VEC) \
+            case (RR - 1) * 4 + (RAW ? 2 : 0) + (VEC ? 1 : 0): \
+                smooth2d_kernel<RR, RAW, VEC><<<grid, 256, 0, stream>>>(vb, g1, g2, wbuf32, wint, ob, pv, pi, rpv, rpi); \
+                break;
+            MCD_SMOOTH2D(1, false, false) MCD_SMOOTH2D(1, false, true) MCD_SMOOTH2D(1, true, false) MCD_SMOOTH2D(1, true, true)
+            MCD_SMOOTH2D(2, false, false) MCD_SMOOTH2D(2, false, true) MCD_SMOOTH2D(2, true, false) MCD_SMOOTH2D(2, true, true)
+            MCD_SMOOTH2D(3, false, false) MCD_SMOOTH2D(3, false, true) MCD_SMOOTH2D(3, true, false) MCD_SMOOTH2D(3, true, true)
+#undef MCD_SMOOTH2D
+            default: return cudaErrorInvalidValue;
         }
     } else {
         dim3 grid(nb, n_scen);
