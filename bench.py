@@ -476,6 +476,86 @@ def c4_search(pkg, ctx):
             "p_hat": p_hat}
 
 
+def paper_problem(pkg, ctx, n_alpha=2000, N1=10240, N2=20480):
+    """One optimisation problem of the paper at its own sizes (Sec. 2.2-3):
+    n_alpha alpha points, each estimated by the two-layer estimator with N1
+    prior samples crossed with N2 inner draws (strong-biomarker condition,
+    d = 3); all outer samples share the inner draws, so the shared-draw
+    kernel evaluates N1 * N2 pairs per alpha point from N2 draws."""
+    import torch
+
+    import workloads
+    a = workloads.paper_two_layer_arrays("c", N1=N1, N2=N2, alphas=workloads.paper_alpha_points("c", n_alpha), seed=0)
+    J, d = a["mu"].shape
+    f64 = torch.float64
+    t0 = time.perf_counter()
+    dp = pkg.DeviceProblem(np.array([d], np.int32), np.zeros(J, np.int32), np.full(J, N2, np.uint64),
+                           np.zeros(J, np.uint64), torch.as_tensor(a["sigma"].ravel(), dtype=f64, device="cuda"),
+                           torch.as_tensor(a["mu"].ravel(), dtype=f64, device="cuda"),
+                           torch.as_tensor(a["b"].ravel(), dtype=f64, device="cuda"))
+    plan = pkg.Plan(ctx, dp, shared=True)
+    plan_s = time.perf_counter() - t0
+    plan.eval(1)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    out = plan.eval(2)
+    ev[1].record()
+    ev[1].synchronize()
+    ms = ev[0].elapsed_time(ev[1])
+    ctx.sync_status()
+    p_first = float(out["p"][:N1].mean().item())
+    plan.close()
+    del dp, out
+    # the same alpha point by the per-design kernel (every design draws its own copy of the stream)
+    one = workloads.paper_two_layer("c", N1=N1, N2=N2, seed=0, key=0)
+    odp = pkg.DeviceProblem.from_workload(one)
+    per = pkg.Plan(ctx, odp)
+    per.eval(1)
+    ev[0].record()
+    per.eval(2)
+    ev[1].record()
+    ev[1].synchronize()
+    per_ms = ev[0].elapsed_time(ev[1])
+    per.close()
+    torch.cuda.empty_cache()
+    pairs = float(J) * N2
+    return {"alpha_points": n_alpha, "N1": N1, "N2": N2, "pairs": pairs, "ms": ms,
+            "pair_evals_per_s": pairs / (ms / 1e3), "plan_build_s": plan_s,
+            "per_design_kernel_ms_per_alpha_point": per_ms,
+            "per_design_kernel_ms_per_problem_extrapolated": per_ms * n_alpha,
+            "p_hat_first_alpha_point": p_first,
+            "paper_context": "mean 31.6 s per problem for the whole optimisation on a V100 (Sec. 3; 4.5 h / 513 problems)"}
+
+
+def c2_shared(pkg, ctx, c2):
+    """The d=3 grid's common-random-number groups (one stream per scenario)
+    evaluated by the shared-draw kernel, forward and forward + adjoint,
+    against the per-design kernel on the same seed (hits must agree)."""
+    import torch
+    dp = pkg.DeviceProblem.from_workload(c2)
+    jac = torch.as_tensor(c2.jac_packed(), dtype=torch.float64, device="cuda")
+    res = {}
+    ref = pkg.Plan(ctx, dp)
+    ref_hits = ref.eval(77)["hits"].clone()
+    ref.close()
+    for grad in (False, True):
+        plan = pkg.Plan(ctx, dp, shared=True, grad=grad, k=4 if grad else 0)
+        run = (lambda s: plan.grad(s, jac, 0.01)) if grad else (lambda s: plan.eval(s))
+        run(76)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        out = run(77)
+        ev[1].record()
+        ev[1].synchronize()
+        ms = ev[0].elapsed_time(ev[1])
+        same = bool(torch.equal(out["hits"], ref_hits))
+        res["adj" if grad else "fwd"] = {"ms": ms, "draw_evals_per_s": c2.total_draws() / (ms / 1e3),
+                                         "hits_equal_per_design_kernel": same}
+        plan.close()
+    ctx.sync_status()
+    return res
+
+
 def run_extras(pkg, ctx, c2):
     import torch
 
@@ -499,6 +579,10 @@ def run_extras(pkg, ctx, c2):
     ex["c3"] = c3_batched_vs_per_design(pkg, ctx)
     # d=10 gradient search (120 adjoint launches of 1e7 draws)
     ex["c4_search"] = c4_search(pkg, ctx)
+    # the d=3 grid by the shared-draw kernel (one stream per scenario)
+    ex["c2_shared"] = c2_shared(pkg, ctx, c2)
+    # one of the paper's optimisation problems at its own sizes (two-layer estimator)
+    ex["paper_problem"] = paper_problem(pkg, ctx)
     # smoothing at scale: 4096 scenarios x 256 x 256 FP64 grids
     S, G = 4096, 256
     v = torch.rand(S * G * G, dtype=torch.float64, device="cuda")

@@ -100,3 +100,57 @@ def collapsed_prior(r, I3, Delta0, prior_sd_scale=80.0 / 4.0):
     Sp = Sig * np.outer(sd, sd)
     S = np.sqrt(r * I3)
     return S * theta, Sig + np.outer(S, S) * Sp
+
+
+def two_layer_moments(r, alpha, I3, Delta0, prior_sd_scale=80.0 / 4.0):
+    """Moments of the indicator of the paper's two-layer estimator (Sec. 2.2).
+
+    Eq. 5-7 average h(theta_k, x_l) = 1{some x_l,i + S_i theta_k,i > b_i} over
+    all pairs of N1 outer samples theta_k ~ N(theta_bar, Sigma_p) (the prior
+    of Eq. 10 on the log hazard ratio) and N2 inner samples x_l ~ N(0, Sigma(r))
+    (Eq. 1), with S = diag(sqrt(r_i I3)) and b_i = Z_{1 - alpha_i}.
+    Returns (P, s2, s_theta2, s_x2):
+      P        = E h = 1 - Phi_C(b - S theta_bar),  C = Sigma + S Sigma_p S;
+      s2       = Var h = P (1 - P);
+      s_theta2 = Var_theta E_x h  (two draws sharing theta: Cov = S Sigma_p S);
+      s_x2     = Var_x E_theta h  (two draws sharing x:     Cov = Sigma).
+    E[h h'] for a shared component is 1 - 2 (1 - P) + Phi_6(b - m, b - m) of
+    the stacked 2d-vector; the 2d-dimensional normal CDF is scipy's (Genz)
+    routine, the d-dimensional orthant the quadrature of quad.orthant.
+    """
+    from scipy.stats import multivariate_normal
+    r = np.asarray(r, dtype=np.float64)
+    d = r.shape[0]
+    Sig = np.empty((d, d))
+    for k in range(d):
+        for l in range(d):
+            lo, hi = min(r[k], r[l]), max(r[k], r[l])
+            Sig[k, l] = math.sqrt(lo / hi)
+    theta = -np.log1p(-np.asarray(Delta0, dtype=np.float64))
+    sd = 1.0 / np.sqrt(prior_sd_scale * r)
+    S = np.sqrt(r * I3)
+    SSpS = np.outer(S, S) * Sig * np.outer(sd, sd)
+    C = Sig + SSpS
+    t = quad.norm_ppf(1.0 - np.asarray(alpha, dtype=np.float64)) - S * theta
+    F = quad.orthant(t, C)
+    P = 1.0 - F
+
+    def both(cross):
+        big = np.block([[C, cross], [cross.T, C]])
+        kw = dict(mean=np.zeros(2 * d), cov=big, abseps=1e-7, releps=1e-7, maxpts=2_000_000 * d)
+        try:
+            F2 = multivariate_normal.cdf(np.concatenate([t, t]), rng=np.random.default_rng(0), **kw)
+        except TypeError:                                   # scipy without the rng keyword
+            F2 = multivariate_normal.cdf(np.concatenate([t, t]), **kw)
+        return 1.0 - 2.0 * F + F2
+
+    return P, P * (1.0 - P), both(SSpS) - P * P, both(Sig) - P * P
+
+
+def two_layer_variance(N1, N2, moments):
+    """Exact variance of the Eq. 7 estimator (a two-sample U-statistic): pairs
+    that share theta_k covary by s_theta2, pairs that share x_l by s_x2, so
+    Var = [s2 + (N2 - 1) s_theta2 + (N1 - 1) s_x2] / (N1 N2).  Appendix A.2's
+    bound 1/(4 N1 N2) covers only the first term."""
+    _, s2, sth, sx = moments
+    return (s2 + (N2 - 1) * sth + (N1 - 1) * sx) / (N1 * N2)

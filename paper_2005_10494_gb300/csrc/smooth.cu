@@ -10,8 +10,10 @@
 // linear stencil for each pair of edge classes (distance to the low and high
 // edge, capped at the reach R), so the FP64 solve runs once per class pair
 // and the application over the grid is a stencil, HBM-bound, in FP32.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
+
 
 #include "mcd_internal.cuh"
 
@@ -329,43 +331,35 @@ __device__ __forceinline__ void stage_rows(const unsigned long long* __restrict_
     }
 }
 
-// 2-D stencil: one block = kRowsPerBlock x kColsPerBlock outputs of one
-// scenario, 256 threads.  The input window is staged as FP32 (stage_rows, in
-// three batches of rows, each with all its loads in flight at once).  Thread
-// (tx, ty) owns the 4 x 4 outputs at rows 4 ty.., columns 4 tx..; it applies
-// the interior stencil to all of them, streaming the 4 + 2R rows of its
-// window through registers with 16-byte shared loads, and keeps the outputs
-// whose edge class is interior.  The block's edge outputs (fewer than R
-// points to a grid edge) follow, one per thread, with their class stencils.
-// VEC: g2 even and the input 16-byte aligned (pairs of doubles per load).
-template <int R, bool RAW, bool VEC>
-__global__ void __launch_bounds__(256, 4) smooth2d_kernel(const unsigned long long* __restrict__ val, int g1, int g2,
-                                                       const float* __restrict__ w32, const float* __restrict__ wint,
-                                                       unsigned long long* __restrict__ out,
-                                                       unsigned long long* part_v, long long* part_i,
-                                                       unsigned long long* rpart_v, long long* rpart_i) {
-    constexpr int T = 2 * R + 1;
-    constexpr int SR = kRowsPerBlock + 2 * R;               // staged rows
-    constexpr int NIC = 4 + 2 * R;                          // input columns of a thread's window
-    constexpr int NV = (NIC + 3) / 4;                       // 16-byte loads per window row
-    constexpr int SCP = 4 * 31 + 4 * NV;                    // shared row stride (floats)
-    constexpr int RPW = (SR + 7) / 8;                       // staged rows per warp
-    __shared__ __align__(16) float tile[SR][SCP];
-    __shared__ unsigned long long sv[8];
-    __shared__ long long si[8];
-    __shared__ float sm_max[8];
-    __shared__ long long sm_idx;
-    const int s = blockIdx.z;
-    const int r0 = blockIdx.y * kRowsPerBlock, c0 = blockIdx.x * kColsPerBlock;
-    const unsigned long long* V = val + static_cast<int64_t>(s) * g1 * g2;
-    RunMax raw;
-    raw.init();
-    static_assert(RPW == 5, "staging batches assume 5 rows per warp");
-    stage_rows<R, RAW, VEC, 0, 2, SR, SCP>(V, g1, g2, r0, c0, tile, raw);
-    stage_rows<R, RAW, VEC, 2, 4, SR, SCP>(V, g1, g2, r0, c0, tile, raw);
-    stage_rows<R, RAW, VEC, 4, 5, SR, SCP>(V, g1, g2, r0, c0, tile, raw);
-    __syncthreads();
+// Shape constants of the 2-D kernels for reach R.
+template <int R>
+struct Tile2D {
+    static constexpr int T = 2 * R + 1;
+    static constexpr int SR = kRowsPerBlock + 2 * R;        // staged rows
+    static constexpr int NV = (4 + 2 * R + 3) / 4;          // 16-byte loads per window row
+    static constexpr int SCP = 4 * 31 + 4 * NV;             // FP32 tile row stride (floats)
+    static constexpr int RPW = (SR + 7) / 8;                // staged rows per warp
+};
 
+constexpr int kWarps2D = 8;           // argmax candidates per 2-D tile (one per warp)
+
+// Outputs of one staged tile (rows r0.., columns c0.. of scenario s): the
+// interior stencil for every thread's 4 x 4 patch (thread (tx, ty) owns rows
+// 4 ty.., columns 4 tx..; the 4 + 2R rows of its window stream through
+// registers with 16-byte shared loads), kept where the edge class is
+// interior; then the tile's edge outputs (fewer than R points to a grid
+// edge), one per thread, with their class stencils; then the tile's argmax
+// candidates (smoothed, and raw when RAW), one per warp, at slot `slot` of
+// scenario s.
+template <int R, bool RAW>
+__device__ __forceinline__ void tile_outputs(float (*tile)[Tile2D<R>::SCP], int g1, int g2, int s, int r0, int c0,
+                                             const float* __restrict__ w32, const float* __restrict__ wint,
+                                             unsigned long long* __restrict__ out, int nb, int slot,
+                                             unsigned long long* part_v, long long* part_i,
+                                             unsigned long long* rpart_v, long long* rpart_i,
+                                             RunMax& raw) {
+    constexpr int T = Tile2D<R>::T;
+    constexpr int NV = Tile2D<R>::NV;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int orow = r0 + 4 * ty, ocol = c0 + 4 * tx;       // first output of this thread
     const int ncls = (R + 1) * (R + 1);
@@ -377,16 +371,21 @@ __global__ void __launch_bounds__(256, 4) smooth2d_kernel(const unsigned long lo
     // at the canonical positions (R + a, R + b), a <= b.
     float acc[4][4];
     {
+        // packed FP32 FMAs (two lanes per instruction): output columns
+        // (j, j + 1) of a row share one accumulator pair, and input pairs
+        // (in[k], in[k + 1]) of the window row feed them
         constexpr int NC = (R + 1) * (R + 2) / 2;
-        float wc[NC];
+        float2 wc[NC];
 #pragma unroll
         for (int a = 0, n = 0; a <= R; ++a)
 #pragma unroll
-            for (int b = a; b <= R; ++b, ++n) wc[n] = __ldg(&wint[(R + a) * T + (R + b)]);
+            for (int b = a; b <= R; ++b, ++n) {
+                const float w = __ldg(&wint[(R + a) * T + (R + b)]);
+                wc[n] = make_float2(w, w);
+            }
+        float2 acc2[4][2];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+        for (int i = 0; i < 4; ++i) { acc2[i][0] = make_float2(0.0f, 0.0f); acc2[i][1] = make_float2(0.0f, 0.0f); }
 #pragma unroll
         for (int ir = 0; ir < 4 + 2 * R; ++ir) {
             float in[4 * NV];
@@ -396,21 +395,29 @@ __global__ void __launch_bounds__(256, 4) smooth2d_kernel(const unsigned long lo
                 const float4 q = src[v];
                 in[4 * v] = q.x; in[4 * v + 1] = q.y; in[4 * v + 2] = q.z; in[4 * v + 3] = q.w;
             }
+            float2 pr[4 * NV - 1];
+#pragma unroll
+            for (int k = 0; k + 1 < 4 * NV; ++k) pr[k] = make_float2(in[k], in[k + 1]);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int dx = ir - i;                      // window row of output row i
                 if (dx < 0 || dx >= T) continue;
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
+                for (int jp = 0; jp < 2; ++jp)
 #pragma unroll
                     for (int dy = 0; dy < T; ++dy) {
                         const int u = dx < R ? R - dx : dx - R, v = dy < R ? R - dy : dy - R;
                         const int a = u < v ? u : v, b = u < v ? v : u;
                         // canonical index of (a, b): rows a' < a hold R + 1 - a' entries
                         const int n = a * (R + 1) - a * (a - 1) / 2 + (b - a);
-                        acc[i][j] = fmaf(wc[n], in[j + dy], acc[i][j]);
+                        acc2[i][jp] = __ffma2_rn(wc[n], pr[2 * jp + dy], acc2[i][jp]);
                     }
             }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            acc[i][0] = acc2[i][0].x; acc[i][1] = acc2[i][0].y;
+            acc[i][2] = acc2[i][1].x; acc[i][3] = acc2[i][1].y;
         }
     }
     {
@@ -418,7 +425,7 @@ __global__ void __launch_bounds__(256, 4) smooth2d_kernel(const unsigned long lo
 #pragma unroll
         for (int j = 0; j < 4; ++j) col_int[j] = ocol + j >= R && ocol + j <= g2 - 1 - R;
         const bool all_cols = col_int[0] && col_int[3];
-        const bool vec_out = VEC && (reinterpret_cast<uintptr_t>(O) & 15u) == 0;
+        const bool vec_out = (g2 % 2) == 0 && (reinterpret_cast<uintptr_t>(O) & 15u) == 0;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const bool row_int = orow + i >= R && orow + i <= g1 - 1 - R;
@@ -445,9 +452,11 @@ __global__ void __launch_bounds__(256, 4) smooth2d_kernel(const unsigned long lo
             for (int j = 0; j < 4; ++j) best = fmaxf(best, (row_int && col_int[j]) ? acc[i][j] : -INFINITY);
         }
     }
-    // The block's edge outputs (fewer than R rows or columns to a grid edge),
+    // The tile's edge outputs (fewer than R rows or columns to a grid edge),
     // one per thread, with the stencil of their edge class: edge columns (all
-    // rows of the block) first, then edge rows (the other columns).
+    // rows of the tile) first, then edge rows (the other columns).  They are
+    // handed out from the last thread down: the last warps stage one row
+    // fewer.
     float eb_v = -INFINITY;
     long long eb_i = -1;
     {
@@ -460,7 +469,7 @@ __global__ void __launch_bounds__(256, 4) smooth2d_kernel(const unsigned long lo
         const int nec = nl + nr, ner = nt + nbm;
         const int rows_here = min(kRowsPerBlock, g1 - r0);
         const int n1 = nec * rows_here, n2 = ner * kColsPerBlock;
-        for (int t = threadIdx.x; t < n1 + n2; t += blockDim.x) {
+        for (int t = static_cast<int>(blockDim.x) - 1 - static_cast<int>(threadIdx.x); t < n1 + n2; t += blockDim.x) {
             int r, c;
             if (t < n1) {
                 const int e = t / rows_here;
@@ -485,49 +494,74 @@ __global__ void __launch_bounds__(256, 4) smooth2d_kernel(const unsigned long lo
         }
     }
     best = fmaxf(best, eb_v);
-    // Argmax: the block's largest value first (max reductions only), then the
-    // lowest index holding it, searched by the few threads that hold it.
-    long long best_i;
+    // Argmax over the warp's outputs, without block barriers: the largest
+    // value by max reductions, then the lowest index (within the grid,
+    // below 2^31) holding it; one candidate per warp and tile, folded in
+    // index order by argmax_kernel.
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t q = (static_cast<int64_t>(s) * nb + slot) * kWarps2D + warp;
     {
         float m = best;
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if ((threadIdx.x & 31) == 0) sm_max[threadIdx.x >> 5] = m;
-        if (threadIdx.x == 0) sm_idx = -1;
-        __syncthreads();
-        float bm = sm_max[0];
-#pragma unroll
-        for (int w = 1; w < 8; ++w) bm = fmaxf(bm, sm_max[w]);
-        if (best == bm && bm > -INFINITY) {
-            long long cand = (eb_v == bm) ? eb_i : -1;
+        unsigned cand = 0xffffffffu;
+        if (best == m && m > -INFINITY) {
+            if (eb_v == m) cand = static_cast<unsigned>(eb_i);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const bool row_int = orow + i >= R && orow + i <= g1 - 1 - R;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const bool v = row_int && ocol + j >= R && ocol + j <= g2 - 1 - R && acc[i][j] == bm;
-                    const long long idx = static_cast<long long>(orow + i) * g2 + ocol + j;
-                    if (v && (cand < 0 || idx < cand)) cand = idx;
+                    const bool v = row_int && ocol + j >= R && ocol + j <= g2 - 1 - R && acc[i][j] == m;
+                    const unsigned idx = static_cast<unsigned>(orow + i) * static_cast<unsigned>(g2) + static_cast<unsigned>(ocol + j);
+                    if (v && idx < cand) cand = idx;
                 }
             }
-            if (cand >= 0) atomicMin(reinterpret_cast<unsigned long long*>(&sm_idx), static_cast<unsigned long long>(cand));
         }
-        __syncthreads();
-        best_i = sm_idx;
-        best = bm;
-    }
-    const int nb = gridDim.x * gridDim.y;
-    const int b = blockIdx.y * gridDim.x + blockIdx.x;
-    if (threadIdx.x == 0) {
-        part_v[static_cast<int64_t>(s) * nb + b] = best_i >= 0 ? order_key(f2d_bits(best)) : 0ull;
-        part_i[static_cast<int64_t>(s) * nb + b] = best_i;
+        const unsigned wi = __reduce_min_sync(0xffffffffu, cand);
+        if (lane == 0) {
+            part_v[q] = wi != 0xffffffffu ? order_key(f2d_bits(m)) : 0ull;
+            part_i[q] = wi != 0xffffffffu ? static_cast<long long>(wi) : -1ll;
+        }
     }
     if constexpr (RAW) {
         unsigned long long raw_k = raw.key;
         long long raw_i = raw.idx;
-        block_amax(raw_k, raw_i, sv, si);
-        if (threadIdx.x == 0) { rpart_v[static_cast<int64_t>(s) * nb + b] = raw_k; rpart_i[static_cast<int64_t>(s) * nb + b] = raw_i; }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, raw_k, o);
+            const long long i2 = __shfl_xor_sync(0xffffffffu, raw_i, o);
+            amax(raw_k, raw_i, k2, i2);
+        }
+        if (lane == 0) { rpart_v[q] = raw_k; rpart_i[q] = raw_i; }
     }
+}
+
+// 2-D stencil, one block per tile of kRowsPerBlock x kColsPerBlock outputs,
+// 256 threads.  The input window is staged as FP32 through registers
+// (stage_rows, in three batches of rows, each with all its loads in flight
+// at once), then tile_outputs.  VEC: g2 even and the input 16-byte aligned
+// (pairs of doubles per load).
+template <int R, bool RAW, bool VEC>
+__global__ void __launch_bounds__(256, 4) smooth2d_kernel(const unsigned long long* __restrict__ val, int g1, int g2,
+                                                       const float* __restrict__ w32, const float* __restrict__ wint,
+                                                       unsigned long long* __restrict__ out,
+                                                       unsigned long long* part_v, long long* part_i,
+                                                       unsigned long long* rpart_v, long long* rpart_i) {
+    using TS = Tile2D<R>;
+    __shared__ __align__(16) float tile[TS::SR][TS::SCP];
+    const int s = blockIdx.z;
+    const int r0 = blockIdx.y * kRowsPerBlock, c0 = blockIdx.x * kColsPerBlock;
+    const unsigned long long* V = val + static_cast<int64_t>(s) * g1 * g2;
+    RunMax raw;
+    raw.init();
+    static_assert(TS::RPW == 5, "staging batches assume 5 rows per warp");
+    stage_rows<R, RAW, VEC, 0, 2, TS::SR, TS::SCP>(V, g1, g2, r0, c0, tile, raw);
+    stage_rows<R, RAW, VEC, 2, 4, TS::SR, TS::SCP>(V, g1, g2, r0, c0, tile, raw);
+    stage_rows<R, RAW, VEC, 4, 5, TS::SR, TS::SCP>(V, g1, g2, r0, c0, tile, raw);
+    __syncthreads();
+    tile_outputs<R, RAW>(tile, g1, g2, s, r0, c0, w32, wint, out, gridDim.x * gridDim.y,
+                         blockIdx.y * gridDim.x + blockIdx.x, part_v, part_i, rpart_v, rpart_i, raw);
 }
 
 // 1-D stencil along a line of n points.
@@ -578,7 +612,8 @@ __global__ void __launch_bounds__(256) smooth1d_kernel(const unsigned long long*
     if (threadIdx.x == 0) { rpart_v[static_cast<int64_t>(s) * nb + blockIdx.x] = raw_v; rpart_i[static_cast<int64_t>(s) * nb + blockIdx.x] = raw_i; }
 }
 
-// One block per scenario: fold the per-block candidates in index order.
+// One block per scenario: fold its argmax candidates (largest key, then
+// lowest index, so the order of the candidates does not matter).
 __global__ void argmax_kernel(int nb, const unsigned long long* part_v, const long long* part_i,
                               const unsigned long long* rpart_v, const long long* rpart_i, int64_t* idx,
                               double* v, int64_t* ridx, double* rv) {
@@ -607,6 +642,14 @@ __global__ void argmax_kernel(int nb, const unsigned long long* part_v, const lo
     }
 }
 
+int blocks_per_scen(int g1, int g2);
+
+// Argmax candidates of one scenario: one per block (1-D), one per warp and
+// tile (2-D).
+int candidates_per_scen(int g1, int g2) {
+    return (g1 == 1 || g2 == 1) ? blocks_per_scen(g1, g2) : blocks_per_scen(g1, g2) * kWarps2D;
+}
+
 int blocks_per_scen(int g1, int g2) {
     if (g1 == 1 || g2 == 1) {
         const int n = g1 * g2;
@@ -621,9 +664,9 @@ size_t smooth_weight_count() {
     return static_cast<size_t>(kClassSlots) * kMaxTaps + kIntSlot;
 }
 
-// Per-block argmax candidates: smoothed then raw, n_scen * blocks each.
+// Argmax candidates: smoothed then raw, n_scen * candidates_per_scen each.
 size_t smooth_candidate_count(int n_scen, int g1, int g2) {
-    return 2 * static_cast<size_t>(n_scen) * blocks_per_scen(g1, g2);
+    return 2 * static_cast<size_t>(n_scen) * candidates_per_scen(g1, g2);
 }
 
 // wbuf / wbuf32: stencil weights (smooth_weight_count() each); part_val /
@@ -642,10 +685,11 @@ cudaError_t smooth_argmax(int n_scen, int g1, int g2, const double* value, doubl
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int nb = blocks_per_scen(g1, g2);
+    const int ncand = candidates_per_scen(g1, g2);
     unsigned long long* pv = reinterpret_cast<unsigned long long*>(part_val);
     long long* pi = reinterpret_cast<long long*>(part_idx);
-    unsigned long long* rpv = pv + static_cast<size_t>(n_scen) * nb;
-    long long* rpi = pi + static_cast<size_t>(n_scen) * nb;
+    unsigned long long* rpv = pv + static_cast<size_t>(n_scen) * ncand;
+    long long* rpi = pi + static_cast<size_t>(n_scen) * ncand;
     const unsigned long long* vb = reinterpret_cast<const unsigned long long*>(value);
     unsigned long long* ob = reinterpret_cast<unsigned long long*>(smoothed);
     if (two_d) {
@@ -675,7 +719,7 @@ cudaError_t smooth_argmax(int n_scen, int g1, int g2, const double* value, doubl
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    argmax_kernel<<<n_scen, 256, 0, stream>>>(nb, pv, pi, rpv, rpi, argmax_idx, argmax_val, raw_idx, raw_val);
+    argmax_kernel<<<n_scen, 256, 0, stream>>>(ncand, pv, pi, rpv, rpi, argmax_idx, argmax_val, raw_idx, raw_val);
     return cudaGetLastError();
 }
 

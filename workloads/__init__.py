@@ -367,6 +367,67 @@ def paper_optima(n_draws=10_000_000):
                    structures=[{"kind": "dense"}] * 3)
 
 
+# The paper's reported optimal designs (Sec. 3): r, alpha, I3, hazard
+# reductions Delta0 per population, for conditions (a) none, (b) weak and
+# (c) strong biomarker effect.
+PAPER_CONDITIONS = {
+    "a": ([1.0], [0.025], 127.0, [0.25]),
+    "b": ([1.0, 0.365], [0.0163, 0.0107], 211.0, [0.3 - 0.1, 0.3 - 0.1 * 0.365]),
+    "c": ([1.0, 0.446, 0.168], [0.00194, 0.0135, 0.0133], 211.0,
+          [0.8 - 0.6 * 1.0, 0.8 - 0.6 * 0.446, 0.8 - 0.6 * 0.168]),
+}
+
+
+def paper_two_layer_arrays(cond="c", N1=10240, N2=20480, alphas=None, seed=0, key=0, prior_sd_scale=20.0):
+    """Packed inputs of the paper's two-layer estimator (Sec. 2.2, Eq. 5-7).
+
+    Outer layer: N1 effect-size samples from the prior of Eq. 10 on the log
+    hazard ratio, theta_k ~ N(theta_bar, Sigma_p) with theta_bar =
+    -log(1 - Delta0) and Sigma_p = Sigma(r) * (sigma sigma^T), sigma_i =
+    1/sqrt(20 r_i), drawn here with numpy default_rng(seed).  Inner layer: the
+    engine's N2 draws x_l ~ N(0, Sigma(r)) (Eq. 1) of stream `key`, shared by
+    every outer sample (the cross pairing of Eq. 7).  Design (a, k) tests the
+    thresholds b_a = Z_{1 - alpha_a} against x + S theta_k, S = diag(sqrt(r I3)),
+    i.e. mean shift mu = S theta_k.  `alphas` is a list of alpha vectors (the
+    alpha points of one optimisation problem; default: the condition's
+    reported optimum).  Designs are alpha-major: j = a N1 + k.
+    Returns dict(sigma, mu[J, d], b[J, d], n_draws, key)."""
+    r, alpha0, I3v, d0 = PAPER_CONDITIONS[cond]
+    r = np.asarray(r, dtype=np.float64)
+    d = r.shape[0]
+    Sig = nested_sigma(r)
+    theta_bar = -np.log1p(-np.asarray(d0, dtype=np.float64))
+    sd = 1.0 / np.sqrt(prior_sd_scale * r)
+    Lp = np.linalg.cholesky(Sig * np.outer(sd, sd))
+    rng = np.random.default_rng(seed)
+    theta = theta_bar + rng.standard_normal((N1, d)) @ Lp.T
+    mu_k = theta * np.sqrt(r * I3v)
+    A = np.atleast_2d(np.asarray(alpha0 if alphas is None else alphas, dtype=np.float64))
+    b_a = special.ndtri(1.0 - A)
+    mu = np.tile(mu_k, (A.shape[0], 1))
+    b = np.repeat(b_a, N1, axis=0)
+    return {"sigma": Sig, "mu": np.ascontiguousarray(mu), "b": np.ascontiguousarray(b), "n_draws": int(N2),
+            "key": int(key), "cond": cond}
+
+
+def paper_two_layer(cond="c", N1=1024, N2=4096, alphas=None, seed=0, key=0):
+    """paper_two_layer_arrays as a Problem (one scenario, equal keys)."""
+    a = paper_two_layer_arrays(cond, N1, N2, alphas, seed, key)
+    J = a["mu"].shape[0]
+    return Problem("paper-two-layer-" + cond, [a["sigma"]], np.zeros(J, np.int32), list(a["mu"]), list(a["b"]),
+                   np.full(J, a["n_draws"], np.uint64), np.full(J, a["key"], np.uint64),
+                   structures=[{"kind": "dense"}])
+
+
+def paper_alpha_points(cond="c", n=2000, seed=0, total=0.025):
+    """n alpha vectors of a condition's dimension for timing one optimisation
+    problem of the paper (N3 alpha points, Sec. 3): Dirichlet(1) weights
+    scaled to sum `total` (a Bonferroni split of the FWER level)."""
+    d = len(PAPER_CONDITIONS[cond][0])
+    w = np.random.default_rng(seed).dirichlet(np.ones(d), size=n)
+    return total * w
+
+
 def design_at(config, q, a, scenario=0):
     """mu, b, dt/dtheta of one off-grid design of a grid config (for searches)."""
     if config == "c4":
