@@ -556,6 +556,32 @@ def c2_shared(pkg, ctx, c2):
     return res
 
 
+def fwer_calibration(pkg, ctx, n=10_000_000, rounds=14):
+    """Eq. 2 on the device: the alpha scale of every split of the d=3 grid's
+    16 scenarios x 129 allocations, 1e7 draws per evaluation, against the
+    oracle's quadrature calibration (stored tables)."""
+    import torch
+
+    import workloads
+    prob, w, ref, _ = workloads.fwer_calibration("c2", n_draws=n)
+    dp = pkg.DeviceProblem.from_workload(prob)
+    wt = torch.as_tensor(w, dtype=torch.float64, device="cuda")
+    pkg.mc_fwer_calibrate(ctx, dp, wt, workloads.ALPHA0, rounds=rounds, seed=1)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    out = pkg.mc_fwer_calibrate(ctx, dp, wt, workloads.ALPHA0, rounds=rounds, seed=2)
+    ev[1].record()
+    ev[1].synchronize()
+    ctx.sync_status()
+    sc = out["scale"].cpu().numpy()
+    fw = out["fwer"].cpu().numpy()
+    return {"designs": int(prob.n_design), "draws_per_eval": n, "rounds": rounds, "ms": ev[0].elapsed_time(ev[1]),
+            "max_rel_err_scale": float(np.max(np.abs(sc - ref) / ref)),
+            "rms_rel_err_scale": float(np.sqrt(np.mean(((sc - ref) / ref) ** 2))),
+            "max_abs_fwer_minus_alpha0": float(np.max(np.abs(fw - workloads.ALPHA0))),
+            "fwer_se_per_eval": float(np.sqrt(workloads.ALPHA0 * (1 - workloads.ALPHA0) / n))}
+
+
 def run_extras(pkg, ctx, c2):
     import torch
 
@@ -583,6 +609,8 @@ def run_extras(pkg, ctx, c2):
     ex["c2_shared"] = c2_shared(pkg, ctx, c2)
     # one of the paper's optimisation problems at its own sizes (two-layer estimator)
     ex["paper_problem"] = paper_problem(pkg, ctx)
+    # FWER constraint (Eq. 2) solved on the device for every split of the d=3 grid
+    ex["fwer_calibration"] = fwer_calibration(pkg, ctx)
     # smoothing at scale: 4096 scenarios x 256 x 256 FP64 grids
     S, G = 4096, 256
     v = torch.rand(S * G * G, dtype=torch.float64, device="cuda")

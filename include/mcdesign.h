@@ -202,6 +202,36 @@ mcd_status mc_design_grad(mcd_ctx* ctx, const mcd_problem* prob, uint64_t seed,
 mcd_status mc_design_eval_noalloc(int device, const mcd_problem* prob, uint64_t seed,
                                   uint64_t* hits, double* p, double* se, mcd_stream stream);
 
+/* ---- FWER calibration (Eq. 2) ------------------------------------------- */
+
+/* Calibrate each design's alpha split to the family-wise error rate alpha0
+ * on the device.  Eq. 2 constrains the thresholds b_i = Z_{1 - alpha_i} so
+ * that, under the null hypothesis (mu = 0), 1 - Phi_Sigma(b) = alpha0; as in
+ * the paper's reparametrisation (Sec. 2.1) the split w of the alpha budget
+ * is fixed and its scale s solved for: alpha = s w.
+ *   prob: scenarios (DEVICE Sigma), and per design its scenario, stream key,
+ *     draw count and first draw (HOST); prob->mu and prob->b are not read,
+ *     prob->region must be MCD_ANY_EXCEEDS.  Designs whose scenario, key and
+ *     draw range agree share their draws (MCD_PLAN_SHARED).
+ *   w (DEVICE [sum d], layout of mu): the split, w_i >= 0 and finite, some
+ *     w_i > 0; w_i = 0 drops test i (b_i = +inf).  A split that breaks this
+ *     is reported by mcd_sync_status as MCD_EINVAL with the design index, and
+ *     its outputs are NaN.
+ *   alpha0 in (0, 1); rounds in 2..200 evaluation rounds: rounds 0 and 1
+ *     evaluate the Bonferroni bracket [alpha0 / sum w, alpha0 / max w], later
+ *     rounds false-position (Illinois) steps inside it.
+ *   scale (DEVICE [J]): the scale of the last round;  b (DEVICE [sum d]):
+ *     its thresholds Z_{1 - scale w} (also the sampler's thresholds during
+ *     the call);  fwer (DEVICE [J]): the Monte Carlo FWER at that scale.
+ * Every round uses the same draws, so each design's estimated FWER is a
+ * nondecreasing step function of s and the bracket keeps the crossing; the
+ * scale's error is that of the estimate, about
+ * sqrt(alpha0 (1 - alpha0) / N) / (dFWER/ds).  The workspace is allocated
+ * and freed in stream order; not for use under stream capture. */
+mcd_status mc_fwer_calibrate(mcd_ctx* ctx, const mcd_problem* prob, const double* w, double alpha0,
+                             int32_t rounds, uint64_t seed, double* scale, double* b, double* fwer,
+                             mcd_stream stream);
+
 /* ---- smoothing and argmax (Sec. 2.3) ------------------------------------ */
 
 /* Local-polynomial smoothing of n_scen grids of g1 x g2 values (row-major,

@@ -67,6 +67,7 @@ def load(path=LIB_PATH):
         "mc_design_eval": (i32, [vp, ctypes.POINTER(CProblem), u64, vp, vp, vp, vp]),
         "mc_design_grad": (i32, [vp, ctypes.POINTER(CProblem), u64, i32, vp, f64, vp, vp, vp, vp, vp, vp]),
         "mc_smooth_argmax": (i32, [vp, i32, i32, i32, vp, f64, i32, vp, vp, vp, vp, vp, vp]),
+        "mc_fwer_calibrate": (i32, [vp, ctypes.POINTER(CProblem), vp, f64, i32, u64, vp, vp, vp, vp]),
         "mcd_debug_normals": (i32, [vp, u64, u64, u64, u64, vp, vp, vp, vp]),
         "mc_design_eval_noalloc": (i32, [ctypes.c_int, ctypes.POINTER(CProblem), u64, vp, vp, vp, vp]),
     }
@@ -296,6 +297,21 @@ def mc_design_grad(ctx, prob, seed, k=0, jac=None, h=0.0, stream=None):
                                      _ptr(o["hits"]), _ptr(o["p"]), _ptr(o["grad_lr"]), _ptr(o.get("grad_sig")),
                                      _ptr(o["grad_se"]), _stream(stream)))
     return _trim(o, prob.n_design, n)
+
+
+def mc_fwer_calibrate(ctx, prob, w, alpha0=0.025, rounds=14, seed=0, stream=None):
+    """Scale of each design's alpha split w (FP64 CUDA tensor, layout of mu)
+    such that the Monte Carlo FWER under mu = 0 equals alpha0 (Eq. 2);
+    prob.mu and prob.b are not read.  Returns dict scale[J], b[sum d],
+    fwer[J] (device tensors)."""
+    torch = _torch()
+    dev = prob.Sigma.device
+    out = {"scale": torch.empty(max(prob.n_design, 1), dtype=torch.float64, device=dev),
+           "b": torch.empty(max(prob.vec_len, 1), dtype=torch.float64, device=dev),
+           "fwer": torch.empty(max(prob.n_design, 1), dtype=torch.float64, device=dev)}
+    ctx.check(ctx.lib.mc_fwer_calibrate(ctx.handle, ctypes.byref(prob.c), _ptr(w), float(alpha0), int(rounds), seed,
+                                        _ptr(out["scale"]), _ptr(out["b"]), _ptr(out["fwer"]), _stream(stream)))
+    return {"scale": out["scale"][:prob.n_design], "b": out["b"][:prob.vec_len], "fwer": out["fwer"][:prob.n_design]}
 
 
 def mc_smooth_argmax(ctx, values, n_scen, g1, g2, bandwidth=3.0, degree=2, stream=None, smoothed=True,

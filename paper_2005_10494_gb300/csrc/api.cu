@@ -12,6 +12,7 @@
 #include <tuple>
 #include <vector>
 
+#include "fwer.cuh"
 #include "mcd_internal.cuh"
 
 using namespace mcd;
@@ -787,7 +788,7 @@ mcd_status mcd_sync_status(mcd_ctx* ctx, mcd_stream stream) {
     if (st.code == MCD_OK) return MCD_OK;
     const char* what = st.code == MCD_ENOTSPD ? "Sigma is not positive definite (scenario index)"
                        : st.code == MCD_ENAN  ? "NaN in mu or b (design index)"
-                                              : "invalid smoothing window (class index)";
+                                              : "invalid device input: smoothing window (class index) or allocation split (design index)";
     return fail(ctx, st.code, what, st.index);
 }
 
@@ -937,6 +938,71 @@ mcd_status mc_design_grad(mcd_ctx* ctx, const mcd_problem* prob, uint64_t seed, 
     a.g_sig = grad_sig;
     a.g_se = grad_se;
     return one_shot(ctx, prob, k, true, a, stream);
+}
+
+mcd_status mc_fwer_calibrate(mcd_ctx* ctx, const mcd_problem* prob, const double* w, double alpha0, int32_t rounds,
+                             uint64_t seed, double* scale, double* b, double* fwer, mcd_stream stream) {
+    if (!ctx) return MCD_EINVAL;
+    if (!prob) return fail(ctx, MCD_EINVAL, "problem is NULL");
+    if (!(alpha0 > 0.0 && alpha0 < 1.0)) return fail(ctx, MCD_EINVAL, "alpha0 must be in (0, 1)");
+    if (rounds < 2 || rounds > 200) return fail(ctx, MCD_EINVAL, "rounds must be in 2..200");
+    if (prob->region != MCD_ANY_EXCEEDS)
+        return fail(ctx, MCD_EINVAL, "the FWER is the probability that some test rejects: region must be MCD_ANY_EXCEEDS");
+    if (prob->n_design == 0) return MCD_OK;
+    if (!w || !scale || !b || !fwer) return fail(ctx, MCD_EINVAL, "w, scale, b and fwer must not be NULL");
+    if (!is_device_ptr(w) || !is_device_ptr(scale) || !is_device_ptr(b) || !is_device_ptr(fwer))
+        return fail(ctx, MCD_EINVAL, "w, scale, b and fwer must be device memory");
+    if (!prob->scen_d || !prob->design_scen) return fail(ctx, MCD_EINVAL, "scen_d and design_scen must not be NULL");
+    MCD_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    MCD_CUDA(cudaStreamIsCapturing(s, &cs), "cudaStreamIsCapturing");
+    if (cs != cudaStreamCaptureStatusNone) return fail(ctx, MCD_EINVAL, "mc_fwer_calibrate cannot be captured");
+    const int J = prob->n_design;
+    size_t vec_len = 0;
+    for (int j = 0; j < J; ++j) {
+        const int sc = prob->design_scen[j];
+        if (sc < 0 || sc >= prob->n_scen) return fail(ctx, MCD_EINVAL, "design_scen out of range", j);
+        vec_len += static_cast<size_t>(prob->scen_d[sc]);
+    }
+    // the sampler sees mu = 0 (the null hypothesis) and reads its thresholds
+    // from the output array b, which every round rewrites
+    double* mu0 = nullptr;
+    FwerState* st = nullptr;
+    uint64_t* hits = nullptr;
+    double* p = nullptr;
+    MCD_CUDA(cudaMallocAsync(&mu0, sizeof(double) * vec_len, s), "calibration workspace");
+    cudaError_t e = cudaMallocAsync(&st, sizeof(FwerState) * J, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&hits, sizeof(uint64_t) * J, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&p, sizeof(double) * J, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(mu0, 0, sizeof(double) * vec_len, s);
+    mcd_status rc = e == cudaSuccess ? MCD_OK : cuda_fail(ctx, e, "calibration workspace");
+    mcd_problem q = *prob;
+    q.mu = mu0;
+    q.b = b;
+    if (rc == MCD_OK) rc = validate_problem(ctx, &q, 0);
+    mcd_plan pl;
+    pl.stream_ordered = true;
+    pl.alloc_stream = s;
+    if (rc == MCD_OK) rc = plan_build(ctx, &q, MCD_PLAN_SHARED, 0, &pl);
+    if (rc == MCD_OK) {
+        e = launch_fwer_init(J, pl.d_designs, w, alpha0, st, b, ctx->d_status, s);
+        if (e != cudaSuccess) rc = cuda_fail(ctx, e, "calibration launch");
+    }
+    for (int r = 0; r < rounds && rc == MCD_OK; ++r) {
+        LaunchArgs a;
+        a.seed = seed;
+        a.hits = hits;
+        a.p = p;
+        rc = enqueue(&pl, a, s);
+        if (rc != MCD_OK) break;
+        e = launch_fwer_update(J, pl.d_designs, w, p, alpha0, r, r == rounds - 1, st, b, scale, fwer, s);
+        if (e != cudaSuccess) rc = cuda_fail(ctx, e, "calibration launch");
+    }
+    plan_release(&pl);
+    for (void* x : {static_cast<void*>(p), static_cast<void*>(hits), static_cast<void*>(st), static_cast<void*>(mu0)})
+        if (x) cudaFreeAsync(x, s);
+    return rc;
 }
 
 mcd_status mc_smooth_argmax(mcd_ctx* ctx, int32_t n_scen, int32_t g1, int32_t g2, const double* value,

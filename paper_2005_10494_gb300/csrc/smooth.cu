@@ -371,21 +371,16 @@ __device__ __forceinline__ void tile_outputs(float (*tile)[Tile2D<R>::SCP], int 
     // at the canonical positions (R + a, R + b), a <= b.
     float acc[4][4];
     {
-        // packed FP32 FMAs (two lanes per instruction): output columns
-        // (j, j + 1) of a row share one accumulator pair, and input pairs
-        // (in[k], in[k + 1]) of the window row feed them
         constexpr int NC = (R + 1) * (R + 2) / 2;
-        float2 wc[NC];
+        float wc[NC];
 #pragma unroll
         for (int a = 0, n = 0; a <= R; ++a)
 #pragma unroll
-            for (int b = a; b <= R; ++b, ++n) {
-                const float w = __ldg(&wint[(R + a) * T + (R + b)]);
-                wc[n] = make_float2(w, w);
-            }
-        float2 acc2[4][2];
+            for (int b = a; b <= R; ++b, ++n) wc[n] = __ldg(&wint[(R + a) * T + (R + b)]);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) { acc2[i][0] = make_float2(0.0f, 0.0f); acc2[i][1] = make_float2(0.0f, 0.0f); }
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
 #pragma unroll
         for (int ir = 0; ir < 4 + 2 * R; ++ir) {
             float in[4 * NV];
@@ -395,29 +390,21 @@ __device__ __forceinline__ void tile_outputs(float (*tile)[Tile2D<R>::SCP], int 
                 const float4 q = src[v];
                 in[4 * v] = q.x; in[4 * v + 1] = q.y; in[4 * v + 2] = q.z; in[4 * v + 3] = q.w;
             }
-            float2 pr[4 * NV - 1];
-#pragma unroll
-            for (int k = 0; k + 1 < 4 * NV; ++k) pr[k] = make_float2(in[k], in[k + 1]);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int dx = ir - i;                      // window row of output row i
                 if (dx < 0 || dx >= T) continue;
 #pragma unroll
-                for (int jp = 0; jp < 2; ++jp)
+                for (int j = 0; j < 4; ++j)
 #pragma unroll
                     for (int dy = 0; dy < T; ++dy) {
                         const int u = dx < R ? R - dx : dx - R, v = dy < R ? R - dy : dy - R;
                         const int a = u < v ? u : v, b = u < v ? v : u;
                         // canonical index of (a, b): rows a' < a hold R + 1 - a' entries
                         const int n = a * (R + 1) - a * (a - 1) / 2 + (b - a);
-                        acc2[i][jp] = __ffma2_rn(wc[n], pr[2 * jp + dy], acc2[i][jp]);
+                        acc[i][j] = fmaf(wc[n], in[j + dy], acc[i][j]);
                     }
             }
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            acc[i][0] = acc2[i][0].x; acc[i][1] = acc2[i][0].y;
-            acc[i][2] = acc2[i][1].x; acc[i][3] = acc2[i][1].y;
         }
     }
     {

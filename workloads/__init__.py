@@ -321,6 +321,50 @@ def c5(g1=64, g2=64, n_draws=10_000_000, keys="crn"):
                          d, n_draws, keys)
 
 
+def fwer_calibration(config="c2", n_draws=10_000_000, every=1, keys="crn"):
+    """Designs for calibrating alpha splits to the FWER of Eq. 2 on the
+    device: per scenario of `config` (c2: 16 equicorrelated d=3 scenarios;
+    c4: AR(1) d=10; c5: block d=20) one design per allocation a on every
+    `every`-th point of the stored table's grid, with split
+    w(a) = (1 - a, a/(d-1), ...).  mu and b are placeholders (the
+    calibration does not read them).  Returns (Problem, w packed [sum d],
+    reference scales from the table, which the oracle wrote, allocations)."""
+    t = tables()
+    if config == "c2":
+        scen = t["c2"]["scenarios"]
+        sigmas = [equicorrelated(3, s["rho"]) for s in scen]
+        structures = [{"kind": "equi", "rho": s["rho"]} for s in scen]
+        grids = [(np.asarray(s["a"]), np.asarray(s["scale"])) for s in scen]
+        d = 3
+    elif config == "c4":
+        c = t["c4"]
+        d = c["d"]
+        sigmas, structures = [ar1(d, c["rho"])], [{"kind": "ar1", "rho": c["rho"]}]
+        grids = [(np.asarray(c["a"]), np.asarray(c["scale"]))]
+    elif config == "c5":
+        c = t["c5"]
+        d = c["d"]
+        sigmas = [block_equicorrelated(c["sizes"], c["rho_in"], c["rho_out"])]
+        structures = [{"kind": "block", "sizes": c["sizes"], "rho_in": c["rho_in"], "rho_out": c["rho_out"]}]
+        grids = [(np.asarray(c["a"]), np.asarray(c["scale"]))]
+    else:
+        raise ValueError(config)
+    mus, bs, scen_of, ws, ref, alloc, key_list = [], [], [], [], [], [], []
+    for s, (a_grid, s_grid) in enumerate(grids):
+        for i in range(0, len(a_grid), every):
+            ws.append(alloc_weights(float(a_grid[i]), d))
+            ref.append(float(s_grid[i]))
+            alloc.append(float(a_grid[i]))
+            mus.append(np.zeros(d))
+            bs.append(np.zeros(d))
+            scen_of.append(s)
+            key_list.append(s if keys == "crn" else len(mus) - 1)
+    J = len(mus)
+    prob = Problem("fwer-" + config, sigmas, scen_of, mus, bs, np.full(J, n_draws, np.uint64), key_list,
+                   structures=structures)
+    return prob, np.concatenate(ws), np.asarray(ref), np.asarray(alloc)
+
+
 def c5_subsample(n=64, total=4096, seed=0):
     return np.sort(np.random.default_rng(seed).choice(total, n, replace=False))
 
