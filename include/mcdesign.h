@@ -232,6 +232,40 @@ mcd_status mc_fwer_calibrate(mcd_ctx* ctx, const mcd_problem* prob, const double
                              int32_t rounds, uint64_t seed, double* scale, double* b, double* fwer,
                              mcd_stream stream);
 
+/* ---- thin-plate spline smoothing and its maximiser (Sec. 2.3) ---------- */
+
+/* Fit a thin-plate smoothing spline to each of n_surf sets of n_pts
+ * scattered estimates in k = 1..3 dimensions (Sec. 2.3 fits a TPS to the
+ * N3 estimates P_hat(alpha)):
+ *   f(x) = sum_i c_i eta(|x - x_i|) + d_0 + sum_j d_j x_j,
+ *   (K + smoothing I) c + P d = y,  P^T c = 0,  P = [1, x],
+ * eta(r) = r^3 (k = 1), r^2 log r (k = 2), -r (k = 3); smoothing = 0
+ * interpolates.  Solved on the device in FP64: Householder QR of P removes
+ * the side condition, a blocked Cholesky factors the projected system.
+ *   x (DEVICE [n_surf][n_pts][k]), y (DEVICE [n_surf][n_pts]);
+ *   coef (DEVICE [n_surf][n_pts + k + 1]): c_0..c_{n_pts-1}, d_0..d_k;
+ *   fitted (DEVICE [n_surf][n_pts], may be NULL): f at the data, y - smoothing c.
+ * Needs k + 2 <= n_pts <= 16384 and points that P does not make singular
+ * (not all on one line for k = 2, ...).  A system that is not positive
+ * definite after the projection (repeated points with smoothing 0) gives NaN
+ * outputs for that surface and MCD_ENOTSPD with its index at mcd_sync_status.
+ * Workspace n_pts^2 doubles, allocated and freed in stream order; not for use
+ * under stream capture. */
+mcd_status mc_tps_fit(mcd_ctx* ctx, int32_t n_surf, int32_t n_pts, int32_t k, const double* x,
+                      const double* y, double smoothing, double* coef, double* fitted, mcd_stream stream);
+
+/* Maximise each fitted spline inside the box lo <= x <= hi (DEVICE [k] each,
+ * shared by all surfaces), as Sec. 2.3 does with a quasi-Newton method
+ * started at the best fitted point: projected BFGS with Armijo backtracking,
+ * at most `iters` iterations, started at the data point inside the box with
+ * the largest fitted value (lowest index on ties).
+ *   x, coef, fitted: as written by mc_tps_fit;
+ *   x_best (DEVICE [n_surf][k]), f_best (DEVICE [n_surf]): the maximiser and
+ *   f there. */
+mcd_status mc_tps_argmax(mcd_ctx* ctx, int32_t n_surf, int32_t n_pts, int32_t k, const double* x,
+                         const double* coef, const double* fitted, const double* lo, const double* hi,
+                         int32_t iters, double* x_best, double* f_best, mcd_stream stream);
+
 /* ---- smoothing and argmax (Sec. 2.3) ------------------------------------ */
 
 /* Local-polynomial smoothing of n_scen grids of g1 x g2 values (row-major,

@@ -68,6 +68,8 @@ def load(path=LIB_PATH):
         "mc_design_grad": (i32, [vp, ctypes.POINTER(CProblem), u64, i32, vp, f64, vp, vp, vp, vp, vp, vp]),
         "mc_smooth_argmax": (i32, [vp, i32, i32, i32, vp, f64, i32, vp, vp, vp, vp, vp, vp]),
         "mc_fwer_calibrate": (i32, [vp, ctypes.POINTER(CProblem), vp, f64, i32, u64, vp, vp, vp, vp]),
+        "mc_tps_fit": (i32, [vp, i32, i32, i32, vp, vp, f64, vp, vp, vp]),
+        "mc_tps_argmax": (i32, [vp, i32, i32, i32, vp, vp, vp, vp, vp, i32, vp, vp, vp]),
         "mcd_debug_normals": (i32, [vp, u64, u64, u64, u64, vp, vp, vp, vp]),
         "mc_design_eval_noalloc": (i32, [ctypes.c_int, ctypes.POINTER(CProblem), u64, vp, vp, vp, vp]),
     }
@@ -312,6 +314,36 @@ def mc_fwer_calibrate(ctx, prob, w, alpha0=0.025, rounds=14, seed=0, stream=None
     ctx.check(ctx.lib.mc_fwer_calibrate(ctx.handle, ctypes.byref(prob.c), _ptr(w), float(alpha0), int(rounds), seed,
                                         _ptr(out["scale"]), _ptr(out["b"]), _ptr(out["fwer"]), _stream(stream)))
     return {"scale": out["scale"][:prob.n_design], "b": out["b"][:prob.vec_len], "fwer": out["fwer"][:prob.n_design]}
+
+
+def mc_tps_fit(ctx, x, y, smoothing=0.0, stream=None):
+    """Thin-plate smoothing splines of n_surf surfaces: x [n_surf, n_pts, k]
+    and y [n_surf, n_pts] FP64 CUDA tensors.  Returns dict coef
+    [n_surf, n_pts + k + 1] (c then d) and fitted [n_surf, n_pts]."""
+    torch = _torch()
+    if x.dim() != 3 or y.dim() != 2 or x.shape[:2] != y.shape:
+        raise ValueError("x must be [n_surf, n_pts, k] and y [n_surf, n_pts]")
+    S, N, k = (int(v) for v in x.shape)
+    x, y = x.contiguous(), y.contiguous()
+    coef = torch.empty((S, N + k + 1), dtype=torch.float64, device=x.device)
+    fitted = torch.empty((S, N), dtype=torch.float64, device=x.device)
+    ctx.check(ctx.lib.mc_tps_fit(ctx.handle, S, N, k, _ptr(x), _ptr(y), float(smoothing), _ptr(coef), _ptr(fitted),
+                                 _stream(stream)))
+    return {"coef": coef, "fitted": fitted}
+
+
+def mc_tps_argmax(ctx, x, fit, lo, hi, iters=200, stream=None):
+    """Maximiser of each fitted spline (mc_tps_fit's output `fit`) in the box
+    [lo, hi] (FP64 CUDA tensors of k values).  Returns dict x [n_surf, k],
+    f [n_surf]."""
+    torch = _torch()
+    S, N, k = (int(v) for v in x.shape)
+    xb = torch.empty((S, k), dtype=torch.float64, device=x.device)
+    fb = torch.empty(S, dtype=torch.float64, device=x.device)
+    ctx.check(ctx.lib.mc_tps_argmax(ctx.handle, S, N, k, _ptr(x.contiguous()), _ptr(fit["coef"]), _ptr(fit["fitted"]),
+                                    _ptr(lo.contiguous()), _ptr(hi.contiguous()), int(iters), _ptr(xb), _ptr(fb),
+                                    _stream(stream)))
+    return {"x": xb, "f": fb}
 
 
 def mc_smooth_argmax(ctx, values, n_scen, g1, g2, bandwidth=3.0, degree=2, stream=None, smoothed=True,

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "fwer.cuh"
+#include "tps.cuh"
 #include "mcd_internal.cuh"
 
 using namespace mcd;
@@ -1003,6 +1004,58 @@ mcd_status mc_fwer_calibrate(mcd_ctx* ctx, const mcd_problem* prob, const double
     for (void* x : {static_cast<void*>(p), static_cast<void*>(hits), static_cast<void*>(st), static_cast<void*>(mu0)})
         if (x) cudaFreeAsync(x, s);
     return rc;
+}
+
+mcd_status mc_tps_fit(mcd_ctx* ctx, int32_t n_surf, int32_t n_pts, int32_t k, const double* x, const double* y,
+                      double smoothing, double* coef, double* fitted, mcd_stream stream) {
+    if (!ctx) return MCD_EINVAL;
+    if (n_surf < 1) return fail(ctx, MCD_EINVAL, "n_surf must be >= 1");
+    if (k < 1 || k > 3) return fail(ctx, MCD_EINVAL, "k must be 1, 2 or 3");
+    if (n_pts < k + 2 || n_pts > 16384) return fail(ctx, MCD_EINVAL, "n_pts must be in k + 2 .. 16384");
+    if (!(smoothing >= 0.0) || smoothing == INFINITY) return fail(ctx, MCD_EINVAL, "smoothing must be finite and >= 0");
+    if (!x || !y || !coef) return fail(ctx, MCD_EINVAL, "x, y and coef must not be NULL");
+    if (!is_device_ptr(x) || !is_device_ptr(y) || !is_device_ptr(coef) || (fitted && !is_device_ptr(fitted)))
+        return fail(ctx, MCD_EINVAL, "x, y, coef and fitted must be device memory");
+    MCD_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    MCD_CUDA(cudaStreamIsCapturing(s, &cs), "cudaStreamIsCapturing");
+    if (cs != cudaStreamCaptureStatusNone) return fail(ctx, MCD_EINVAL, "mc_tps_fit cannot be captured");
+    const size_t nws = tps_workspace_doubles(n_pts, k);
+    double* ws = nullptr;
+    MCD_CUDA(cudaMallocAsync(&ws, sizeof(double) * (nws + 2), s), "spline workspace");
+    int* bad = reinterpret_cast<int*>(ws + nws);
+    unsigned long long* amax = reinterpret_cast<unsigned long long*>(ws + nws + 1);
+    mcd_status rc = MCD_OK;
+    const int64_t m = k + 1;
+    for (int q = 0; q < n_surf && rc == MCD_OK; ++q) {
+        cudaError_t e = tps_fit_one(x + static_cast<int64_t>(q) * n_pts * k, y + static_cast<int64_t>(q) * n_pts,
+                                    n_pts, k, smoothing, coef + static_cast<int64_t>(q) * (n_pts + m),
+                                    fitted ? fitted + static_cast<int64_t>(q) * n_pts : nullptr, ws, bad, amax,
+                                    ctx->d_status, q, s);
+        if (e != cudaSuccess) rc = cuda_fail(ctx, e, "spline launch");
+    }
+    cudaFreeAsync(ws, s);
+    return rc;
+}
+
+mcd_status mc_tps_argmax(mcd_ctx* ctx, int32_t n_surf, int32_t n_pts, int32_t k, const double* x, const double* coef,
+                         const double* fitted, const double* lo, const double* hi, int32_t iters, double* x_best,
+                         double* f_best, mcd_stream stream) {
+    if (!ctx) return MCD_EINVAL;
+    if (n_surf < 1) return fail(ctx, MCD_EINVAL, "n_surf must be >= 1");
+    if (k < 1 || k > 3) return fail(ctx, MCD_EINVAL, "k must be 1, 2 or 3");
+    if (n_pts < k + 2 || n_pts > 16384) return fail(ctx, MCD_EINVAL, "n_pts must be in k + 2 .. 16384");
+    if (iters < 0 || iters > 100000) return fail(ctx, MCD_EINVAL, "iters must be in 0 .. 100000");
+    const void* ptrs[] = {x, coef, fitted, lo, hi, x_best, f_best};
+    for (const void* p : ptrs) {
+        if (!p) return fail(ctx, MCD_EINVAL, "x, coef, fitted, lo, hi, x_best and f_best must not be NULL");
+        if (!is_device_ptr(p)) return fail(ctx, MCD_EINVAL, "x, coef, fitted, lo, hi, x_best and f_best must be device memory");
+    }
+    MCD_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    MCD_CUDA(tps_argmax(x, coef, fitted, n_surf, n_pts, k, lo, hi, iters, x_best, f_best,
+                        reinterpret_cast<cudaStream_t>(stream)), "spline maximiser launch");
+    return MCD_OK;
 }
 
 mcd_status mc_smooth_argmax(mcd_ctx* ctx, int32_t n_scen, int32_t g1, int32_t g2, const double* value,

@@ -1,0 +1,515 @@
+// Thin-plate spline smoothing of scattered estimates and the maximiser of
+// the fitted surface (Sec. 2.3: the N3 noisy P_hat(alpha) are smoothed by a
+// TPS, whose maximum is found by a quasi-Newton method started at the best
+// fitted point).
+//
+// Fit.  For points x_i in R^k (k = 1, 2, 3), values y_i and smoothing s >= 0
+//   f(x) = sum_i c_i eta(|x - x_i|) + d_0 + sum_j d_j x_j,
+//   (K + s I) c + P d = y,  P^T c = 0,  K_ij = eta(|x_i - x_j|),  P = [1, x],
+// with eta(r) = r^3 (k = 1), r^2 log r (k = 2), -r (k = 3), the radial
+// functions of the second-order spline in k dimensions.  The side condition
+// is removed with the QR factorisation of P by m = k + 1 Householder
+// reflections, Q^T P = [R; 0]: with B = Q^T (K + s I) Q and y~ = Q^T y, the
+// trailing block B22 is positive definite and B22 w = y~_2 gives
+// c = Q [0; w] and R d = y~_1 - B12 w.  B22 is factored by a blocked
+// Cholesky in FP64 (diagonal block in shared memory, panel solve, trailing
+// update), the two triangular systems by row-oriented substitution.  The
+// fitted values at the data are y - s c.
+//
+// Maximiser.  One block per surface: projected BFGS on -f inside a box
+// (Armijo backtracking along the projected path), started at the data point
+// with the largest fitted value inside the box; f and its gradient are block
+// reductions over the N centres.
+#include <cmath>
+#include <cstdint>
+
+#include "tps.cuh"
+
+namespace mcd {
+
+namespace {
+
+constexpr int kNb = 32;            // Cholesky block
+constexpr int kSyrkTile = 64;      // trailing-update tile (64 x 64 outputs per block)
+
+__device__ __forceinline__ double eta(double r, int k) {
+    if (k == 1) return r * r * r;
+    if (k == 2) return r > 0.0 ? r * r * log(r) : 0.0;
+    return -r;
+}
+
+// eta'(r) / r, the factor of (x - x_i) in the gradient (0 at r = 0)
+__device__ __forceinline__ double deta_over_r(double r, int k) {
+    if (k == 1) return 3.0 * r;
+    if (k == 2) return r > 0.0 ? 2.0 * log(r) + 1.0 : 0.0;
+    return r > 0.0 ? -1.0 / r : 0.0;
+}
+
+template <int NT>
+__device__ double block_sum(double v, double* red) {
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < NT / 32; ++w) s += red[w];
+    return s;
+}
+
+__global__ void assemble_kernel(double* __restrict__ A, const double* __restrict__ x, int N, int k, double s) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (j >= N) return;
+    double r2 = 0.0;
+    for (int q = 0; q < k; ++q) {
+        const double t = x[static_cast<int64_t>(i) * k + q] - x[static_cast<int64_t>(j) * k + q];
+        r2 += t * t;
+    }
+    A[static_cast<int64_t>(i) * N + j] = eta(sqrt(r2), k) + (i == j ? s : 0.0);
+}
+
+// Householder QR of P = [1, x] (N x m) in one block: reflector j is
+// v_j (zero above row j, stored in V[j][.]) with H_j = I - tau_j v_j v_j^T;
+// R (m x m, row-major) and y~ = Q^T y.
+constexpr int kQrThreads = 1024;
+__global__ void __launch_bounds__(kQrThreads) qr_kernel(const double* __restrict__ x, const double* __restrict__ y,
+                                                      int N, int k, double* __restrict__ Pw, double* __restrict__ V,
+                                                      double* __restrict__ tau, double* __restrict__ R,
+                                                      double* __restrict__ yt) {
+    __shared__ double red[kQrThreads / 32];
+    __shared__ double s_alpha;
+    const int m = k + 1;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        Pw[i] = 1.0;
+        for (int q = 0; q < k; ++q) Pw[static_cast<int64_t>(q + 1) * N + i] = x[static_cast<int64_t>(i) * k + q];
+        yt[i] = y[i];
+    }
+    __syncthreads();
+    for (int j = 0; j < m; ++j) {
+        double* col = Pw + static_cast<int64_t>(j) * N;
+        double loc = 0.0;
+        for (int i = j + threadIdx.x; i < N; i += blockDim.x) loc += col[i] * col[i];
+        const double nrm2 = block_sum<kQrThreads>(loc, red);
+        if (threadIdx.x == 0) {
+            const double a0 = col[j];
+            s_alpha = a0 >= 0.0 ? -sqrt(nrm2) : sqrt(nrm2);
+        }
+        __syncthreads();
+        const double alpha = s_alpha;
+        double* v = V + static_cast<int64_t>(j) * N;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) v[i] = i < j ? 0.0 : (i == j ? col[i] - alpha : col[i]);
+        __syncthreads();
+        double lv = 0.0;
+        for (int i = j + threadIdx.x; i < N; i += blockDim.x) lv += v[i] * v[i];
+        const double vv = block_sum<kQrThreads>(lv, red);
+        const double t = vv > 0.0 ? 2.0 / vv : 0.0;
+        if (threadIdx.x == 0) { tau[j] = t; R[j * m + j] = alpha; }
+        // apply H_j to the remaining columns and to y~
+        for (int l = j + 1; l <= m; ++l) {
+            double* u = l < m ? Pw + static_cast<int64_t>(l) * N : yt;
+            double ld = 0.0;
+            for (int i = j + threadIdx.x; i < N; i += blockDim.x) ld += v[i] * u[i];
+            const double dot = block_sum<kQrThreads>(ld, red);
+            for (int i = j + threadIdx.x; i < N; i += blockDim.x) u[i] -= t * dot * v[i];
+            __syncthreads();
+            if (l < m && threadIdx.x == 0) R[j * m + l] = u[j];
+        }
+        if (threadIdx.x < m && threadIdx.x < j) R[j * m + threadIdx.x] = 0.0;
+        __syncthreads();
+    }
+}
+
+// w = A v for the symmetric N x N matrix A (one warp per row).
+__global__ void matvec_kernel(const double* __restrict__ A, const double* __restrict__ v, double* __restrict__ w, int N) {
+    const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= N) return;
+    const double* a = A + static_cast<int64_t>(row) * N;
+    double s = 0.0;
+    for (int j = lane; j < N; j += 32) s += a[j] * v[j];
+    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) w[row] = s;
+}
+
+// u = tau w - (tau^2 v^T w / 2) v, in place in w (one block).
+__global__ void __launch_bounds__(1024) rank2_prep_kernel(const double* __restrict__ v, double* __restrict__ w,
+                                                          const double* __restrict__ tau, int j, int N) {
+    __shared__ double red[32];
+    double l = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) l += v[i] * w[i];
+    const double vw = block_sum<1024>(l, red);
+    const double t = tau[j];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) w[i] = t * w[i] - 0.5 * t * t * vw * v[i];
+}
+
+// A <- H A H = A - v u^T - u v^T.
+__global__ void rank2_kernel(double* __restrict__ A, const double* __restrict__ v, const double* __restrict__ u, int N) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (j >= N) return;
+    A[static_cast<int64_t>(i) * N + j] -= v[i] * u[j] + u[i] * v[j];
+}
+
+// max |A_ij| (non-negative doubles order like their bit patterns).
+__global__ void maxabs_kernel(const double* __restrict__ A, int64_t count, unsigned long long* __restrict__ out) {
+    double m = 0.0;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < count;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        m = fmax(m, fabs(A[i]));
+    for (int o = 16; o >= 1; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, static_cast<unsigned long long>(__double_as_longlong(m)));
+}
+
+// Cholesky of the b x b diagonal block at G (leading dimension ld), lower,
+// in place.  A pivot at or below n eps max|A| (the projected system is
+// singular to working precision, e.g. repeated points without smoothing)
+// sets *bad.
+__global__ void __launch_bounds__(kNb * kNb) chol_diag_kernel(double* __restrict__ G, int64_t ld, int b, int n,
+                                                             const unsigned long long* __restrict__ amax,
+                                                             int* __restrict__ bad) {
+    __shared__ double a[kNb][kNb + 1];
+    const int tx = threadIdx.x % kNb, ty = threadIdx.x / kNb;   // column tx, row ty
+    const double floor_p = static_cast<double>(n) * 2.220446049250313e-16 * __longlong_as_double(static_cast<long long>(*amax));
+    if (ty < b && tx < b) a[ty][tx] = G[static_cast<int64_t>(ty) * ld + tx];
+    __syncthreads();
+    for (int kk = 0; kk < b; ++kk) {
+        if (threadIdx.x == 0) {
+            const double p = a[kk][kk];
+            if (!(p > floor_p)) { *bad = 1; a[kk][kk] = 1.0; }
+            else a[kk][kk] = sqrt(p);
+        }
+        __syncthreads();
+        if (tx == kk && ty > kk && ty < b) a[ty][kk] /= a[kk][kk];
+        __syncthreads();
+        if (ty > kk && tx > kk && tx <= ty && ty < b) a[ty][tx] -= a[ty][kk] * a[tx][kk];
+        __syncthreads();
+    }
+    if (ty < b && tx <= ty) G[static_cast<int64_t>(ty) * ld + tx] = a[ty][tx];
+}
+
+// Rows below the diagonal block: X <- X L^{-T} for the n_rem x b panel at
+// Pn (leading dimension ld), L the factored diagonal block at G.
+__global__ void chol_trsm_kernel(const double* __restrict__ G, double* __restrict__ Pn, int64_t ld, int b, int n_rem) {
+    __shared__ double L[kNb][kNb + 1];
+    for (int t = threadIdx.x; t < kNb * kNb; t += blockDim.x) {
+        const int r = t / kNb, c = t % kNb;
+        L[r][c] = (r < b && c <= r) ? G[static_cast<int64_t>(r) * ld + c] : 0.0;
+    }
+    __syncthreads();
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= n_rem) return;
+    double* p = Pn + static_cast<int64_t>(row) * ld;
+    double xr[kNb];
+#pragma unroll
+    for (int j = 0; j < kNb; ++j) {
+        if (j < b) {
+            double s = p[j];
+#pragma unroll
+            for (int l = 0; l < j; ++l) s -= xr[l] * L[j][l];
+            xr[j] = s / L[j][j];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kNb; ++j)
+        if (j < b) p[j] = xr[j];
+}
+
+// Trailing update of the lower triangle: T[i][j] -= sum_l Pn[i][l] Pn[j][l],
+// i >= j, for the n_rem x n_rem matrix at T and the n_rem x b panel at Pn.
+// Block (bx, by): output tile rows by*64.., columns bx*64..; 256 threads,
+// 4 x 4 outputs each.
+__global__ void __launch_bounds__(256) chol_syrk_kernel(double* __restrict__ T, const double* __restrict__ Pn,
+                                                        int64_t ld, int b, int n_rem) {
+    const int ti = blockIdx.y, tj = blockIdx.x;
+    if (tj > ti) return;
+    __shared__ double si[kSyrkTile][kNb + 1];
+    __shared__ double sj[kSyrkTile][kNb + 1];
+    const int r0 = ti * kSyrkTile, c0 = tj * kSyrkTile;
+    for (int t = threadIdx.x; t < kSyrkTile * kNb; t += blockDim.x) {
+        const int r = t / kNb, l = t % kNb;
+        si[r][l] = (r0 + r < n_rem && l < b) ? Pn[static_cast<int64_t>(r0 + r) * ld + l] : 0.0;
+        sj[r][l] = (c0 + r < n_rem && l < b) ? Pn[static_cast<int64_t>(c0 + r) * ld + l] : 0.0;
+    }
+    __syncthreads();
+    const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+    double acc[4][4] = {};
+    for (int l = 0; l < b; ++l) {
+        double a[4], c[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { a[q] = si[ty + 16 * q][l]; c[q] = sj[tx + 16 * q][l]; }
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[p][q] = fma(a[p], c[q], acc[p][q]);
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = r0 + ty + 16 * p, j = c0 + tx + 16 * q;
+            if (i < n_rem && j < n_rem && j <= i) T[static_cast<int64_t>(i) * ld + j] -= acc[p][q];
+        }
+}
+
+// Solve L z = r (forward, row-oriented) then L^T w = z (backward,
+// column updates by rows of L), in one block; n x n lower factor at L.
+constexpr int kSolveThreads = 1024;
+__global__ void __launch_bounds__(kSolveThreads) chol_solve_kernel(const double* __restrict__ L, int64_t ld, int n,
+                                                                  double* __restrict__ z) {
+    __shared__ double red[kSolveThreads / 32];
+    for (int i = 0; i < n; ++i) {
+        const double* row = L + static_cast<int64_t>(i) * ld;
+        double s = 0.0;
+        for (int j = threadIdx.x; j < i; j += blockDim.x) s += row[j] * z[j];
+        const double tot = block_sum<kSolveThreads>(s, red);
+        if (threadIdx.x == 0) z[i] = (z[i] - tot) / row[i];
+        __syncthreads();
+    }
+    for (int j = n - 1; j >= 0; --j) {
+        const double* row = L + static_cast<int64_t>(j) * ld;
+        if (threadIdx.x == 0) z[j] /= row[j];
+        __syncthreads();
+        const double wj = z[j];
+        for (int i = threadIdx.x; i < j; i += blockDim.x) z[i] -= row[i] * wj;
+        __syncthreads();
+    }
+}
+
+// c = Q [0; w], R d = y~_1 - B12 w, fitted = y - s c; NaN when the
+// factorisation failed.  One block.
+__global__ void __launch_bounds__(1024) combine_kernel(const double* __restrict__ A, const double* __restrict__ V,
+                                                       const double* __restrict__ tau, const double* __restrict__ R,
+                                                       const double* __restrict__ yt, const double* __restrict__ w,
+                                                       const double* __restrict__ y, int N, int k, double s,
+                                                       const int* __restrict__ bad, double* __restrict__ coef,
+                                                       double* __restrict__ fitted, DevStatus* status, int surf) {
+    __shared__ double red[32];
+    __shared__ double rhs[4];
+    const int m = k + 1;
+    const bool ok = *bad == 0;
+    if (!ok) {
+        if (threadIdx.x == 0) set_status(status, MCD_ENOTSPD, surf);
+        for (int i = threadIdx.x; i < N + m; i += blockDim.x) coef[i] = NAN;
+        if (fitted)
+            for (int i = threadIdx.x; i < N; i += blockDim.x) fitted[i] = NAN;
+        return;
+    }
+    // rhs_j = y~_j - sum_l B[j][m + l] w_l
+    for (int j = 0; j < m; ++j) {
+        double l = 0.0;
+        for (int i = threadIdx.x; i < N - m; i += blockDim.x) l += A[static_cast<int64_t>(j) * N + m + i] * w[i];
+        const double t = block_sum<1024>(l, red);
+        if (threadIdx.x == 0) rhs[j] = yt[j] - t;
+        __syncthreads();
+    }
+    // c = H_0 ... H_{m-1} [0; w]
+    for (int i = threadIdx.x; i < N; i += blockDim.x) coef[i] = i < m ? 0.0 : w[i - m];
+    __syncthreads();
+    for (int j = m - 1; j >= 0; --j) {
+        const double* v = V + static_cast<int64_t>(j) * N;
+        double l = 0.0;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) l += v[i] * coef[i];
+        const double dot = block_sum<1024>(l, red);
+        for (int i = threadIdx.x; i < N; i += blockDim.x) coef[i] -= tau[j] * dot * v[i];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double d[4];
+        for (int j = m - 1; j >= 0; --j) {
+            double t = rhs[j];
+            for (int l = j + 1; l < m; ++l) t -= R[j * m + l] * d[l];
+            d[j] = t / R[j * m + j];
+        }
+        for (int j = 0; j < m; ++j) coef[N + j] = d[j];
+    }
+    if (fitted)
+        for (int i = threadIdx.x; i < N; i += blockDim.x) fitted[i] = y[i] - s * coef[i];
+}
+
+// ---- maximiser ---------------------------------------------------------------
+constexpr int kMaxThreads = 256;
+
+// f and its gradient at z (all threads return the same values).
+__device__ void f_and_grad(const double* __restrict__ x, const double* __restrict__ coef, int N, int k,
+                           const double* z, double& f, double* g, double* red) {
+    double lf = 0.0, lg[3] = {0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        double diff[3], r2 = 0.0;
+        for (int q = 0; q < k; ++q) {
+            diff[q] = z[q] - x[static_cast<int64_t>(i) * k + q];
+            r2 += diff[q] * diff[q];
+        }
+        const double r = sqrt(r2), c = coef[i];
+        lf += c * eta(r, k);
+        const double fac = c * deta_over_r(r, k);
+        for (int q = 0; q < k; ++q) lg[q] += fac * diff[q];
+    }
+    f = block_sum<kMaxThreads>(lf, red) + coef[N];
+    for (int q = 0; q < k; ++q) f += coef[N + 1 + q] * z[q];
+    for (int q = 0; q < k; ++q) g[q] = block_sum<kMaxThreads>(lg[q], red) + coef[N + 1 + q];
+}
+
+__global__ void __launch_bounds__(kMaxThreads) argmax_tps_kernel(const double* __restrict__ x,
+                                                                 const double* __restrict__ coef,
+                                                                 const double* __restrict__ fitted, int N, int k,
+                                                                 const double* __restrict__ lo,
+                                                                 const double* __restrict__ hi, int iters,
+                                                                 double* __restrict__ xbest,
+                                                                 double* __restrict__ fbest) {
+    __shared__ double red[kMaxThreads / 32];
+    __shared__ double sbest[kMaxThreads];
+    __shared__ int sidx[kMaxThreads];
+    const int surf = blockIdx.x;
+    const double* X = x + static_cast<int64_t>(surf) * N * k;
+    const double* C = coef + static_cast<int64_t>(surf) * (N + k + 1);
+    const double* F = fitted + static_cast<int64_t>(surf) * N;
+    // start: the data point inside the box with the largest fitted value
+    // (lowest index on ties)
+    double bv = -INFINITY;
+    int bi = -1;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        bool in = true;
+        for (int q = 0; q < k; ++q) {
+            const double t = X[static_cast<int64_t>(i) * k + q];
+            in = in && t >= lo[q] && t <= hi[q];
+        }
+        if (in && F[i] > bv) { bv = F[i]; bi = i; }
+    }
+    sbest[threadIdx.x] = bv;
+    sidx[threadIdx.x] = bi;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int t = 1; t < blockDim.x; ++t)
+            if (sidx[t] >= 0 && (sidx[0] < 0 || sbest[t] > sbest[0] || (sbest[t] == sbest[0] && sidx[t] < sidx[0]))) {
+                sbest[0] = sbest[t];
+                sidx[0] = sidx[t];
+            }
+    }
+    __syncthreads();
+    const int start = sidx[0];
+    double z[3] = {0, 0, 0}, g[3], f;
+    for (int q = 0; q < k; ++q) z[q] = start >= 0 ? X[static_cast<int64_t>(start) * k + q] : 0.5 * (lo[q] + hi[q]);
+    f_and_grad(X, C, N, k, z, f, g, red);
+    // inverse-Hessian approximation of -f (ascent direction H g)
+    double H[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    double scale = 0.0;
+    for (int q = 0; q < k; ++q) scale = fmax(scale, hi[q] - lo[q]);
+    for (int q = 0; q < k; ++q) H[q][q] = 0.1 * scale / fmax(1e-300, sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]));
+    for (int it = 0; it < iters; ++it) {
+        double p[3] = {0, 0, 0};
+        for (int a = 0; a < k; ++a)
+            for (int b = 0; b < k; ++b) p[a] += H[a][b] * g[b];
+        // components that would leave the box at an active bound are dropped
+        for (int q = 0; q < k; ++q)
+            if ((z[q] <= lo[q] && p[q] < 0.0) || (z[q] >= hi[q] && p[q] > 0.0)) p[q] = 0.0;
+        double gp = 0.0;
+        for (int q = 0; q < k; ++q) gp += g[q] * p[q];
+        if (!(gp > 0.0)) {                                       // not an ascent direction: restart along g
+            for (int a = 0; a < k; ++a)
+                for (int b = 0; b < k; ++b) H[a][b] = a == b ? H[a][a] : 0.0;
+            for (int q = 0; q < k; ++q) {
+                p[q] = H[q][q] * g[q];
+                if ((z[q] <= lo[q] && p[q] < 0.0) || (z[q] >= hi[q] && p[q] > 0.0)) p[q] = 0.0;
+            }
+            gp = 0.0;
+            for (int q = 0; q < k; ++q) gp += g[q] * p[q];
+            if (!(gp > 0.0)) break;                              // projected gradient is zero
+        }
+        double t = 1.0, zn[3] = {z[0], z[1], z[2]}, fn = f, gn[3] = {g[0], g[1], g[2]};
+        bool moved = false;
+        for (int ls = 0; ls < 60; ++ls) {
+            for (int q = 0; q < k; ++q) zn[q] = fmin(fmax(z[q] + t * p[q], lo[q]), hi[q]);
+            f_and_grad(X, C, N, k, zn, fn, gn, red);
+            double dz = 0.0, gz = 0.0;
+            for (int q = 0; q < k; ++q) { dz += fabs(zn[q] - z[q]); gz += g[q] * (zn[q] - z[q]); }
+            if (dz == 0.0) break;
+            if (fn >= f + 1e-4 * gz) { moved = true; break; }
+            t *= 0.5;
+        }
+        if (!moved) break;
+        double s[3], yv[3], sy = 0.0;
+        for (int q = 0; q < k; ++q) { s[q] = zn[q] - z[q]; yv[q] = -(gn[q] - g[q]); sy += s[q] * yv[q]; }
+        for (int q = 0; q < k; ++q) { z[q] = zn[q]; g[q] = gn[q]; }
+        const double df = fn - f;
+        f = fn;
+        if (sy > 1e-300) {                                       // BFGS update of the inverse Hessian of -f
+            double Hy[3] = {0, 0, 0}, yHy = 0.0;
+            for (int a = 0; a < k; ++a)
+                for (int b = 0; b < k; ++b) Hy[a] += H[a][b] * yv[b];
+            for (int a = 0; a < k; ++a) yHy += yv[a] * Hy[a];
+            const double rho = 1.0 / sy;
+            for (int a = 0; a < k; ++a)
+                for (int b = 0; b < k; ++b)
+                    H[a][b] += (1.0 + yHy * rho) * rho * s[a] * s[b] - rho * (Hy[a] * s[b] + s[a] * Hy[b]);
+        }
+        if (df <= 1e-16 * fmax(1.0, fabs(f))) break;
+    }
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < k; ++q) xbest[static_cast<int64_t>(surf) * k + q] = z[q];
+        fbest[surf] = f;
+    }
+}
+
+}  // namespace
+
+size_t tps_workspace_doubles(int N, int k) {
+    const size_t m = static_cast<size_t>(k) + 1;
+    return static_cast<size_t>(N) * N + 2 * m * N + 3 * static_cast<size_t>(N) + m * m + m + 8;
+}
+
+cudaError_t tps_fit_one(const double* x, const double* y, int N, int k, double s, double* coef, double* fitted,
+                        double* ws, int* bad, unsigned long long* amax, DevStatus* status, int surf,
+                        cudaStream_t stream) {
+    const int m = k + 1;
+    double* A = ws;
+    double* V = A + static_cast<size_t>(N) * N;
+    double* Pw = V + static_cast<size_t>(m) * N;
+    double* yt = Pw + static_cast<size_t>(m) * N;
+    double* w = yt + N;
+    double* z = w + N;
+    double* R = z + N;
+    double* tau = R + m * m;
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(amax, 0, sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) return e;
+    assemble_kernel<<<dim3((N + 255) / 256, N), 256, 0, stream>>>(A, x, N, k, s);
+    qr_kernel<<<1, kQrThreads, 0, stream>>>(x, y, N, k, Pw, V, tau, R, yt);
+    for (int j = 0; j < m; ++j) {
+        const double* v = V + static_cast<size_t>(j) * N;
+        matvec_kernel<<<(N + 7) / 8, 256, 0, stream>>>(A, v, w, N);
+        rank2_prep_kernel<<<1, 1024, 0, stream>>>(v, w, tau, j, N);
+        rank2_kernel<<<dim3((N + 255) / 256, N), 256, 0, stream>>>(A, v, w, N);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // blocked Cholesky of B22 = A[m:, m:]
+    const int n = N - m;
+    double* B = A + static_cast<size_t>(m) * N + m;
+    maxabs_kernel<<<256, 256, 0, stream>>>(A, static_cast<int64_t>(N) * N, amax);
+    for (int j0 = 0; j0 < n; j0 += kNb) {
+        const int b = n - j0 < kNb ? n - j0 : kNb;
+        double* G = B + static_cast<size_t>(j0) * N + j0;
+        chol_diag_kernel<<<1, kNb * kNb, 0, stream>>>(G, N, b, n, amax, bad);
+        const int rem = n - j0 - b;
+        if (rem > 0) {
+            double* Pn = G + static_cast<size_t>(b) * N;
+            chol_trsm_kernel<<<(rem + 127) / 128, 128, 0, stream>>>(G, Pn, N, b, rem);
+            const int tiles = (rem + kSyrkTile - 1) / kSyrkTile;
+            chol_syrk_kernel<<<dim3(tiles, tiles), 256, 0, stream>>>(Pn + b, Pn, N, b, rem);
+        }
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(z, yt + m, sizeof(double) * n, cudaMemcpyDeviceToDevice, stream)) != cudaSuccess) return e;
+    chol_solve_kernel<<<1, kSolveThreads, 0, stream>>>(B, N, n, z);
+    combine_kernel<<<1, 1024, 0, stream>>>(A, V, tau, R, yt, z, y, N, k, s, bad, coef, fitted, status, surf);
+    return cudaGetLastError();
+}
+
+cudaError_t tps_argmax(const double* x, const double* coef, const double* fitted, int n_surf, int N, int k,
+                       const double* lo, const double* hi, int iters, double* xbest, double* fbest,
+                       cudaStream_t stream) {
+    argmax_tps_kernel<<<n_surf, kMaxThreads, 0, stream>>>(x, coef, fitted, N, k, lo, hi, iters, xbest, fbest);
+    return cudaGetLastError();
+}
+
+}  // namespace mcd
