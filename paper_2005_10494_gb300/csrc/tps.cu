@@ -347,7 +347,7 @@ __device__ void f_and_grad(const double* __restrict__ x, const double* __restric
     }
     f = block_sum<kMaxThreads>(lf, red) + coef[N];
     for (int q = 0; q < k; ++q) f += coef[N + 1 + q] * z[q];
-    for (int q = 0; q < k; ++q) g[q] = block_sum<kMaxThreads>(lg[q], red) + coef[N + 1 + q];
+    for (int q = 0; q < 3; ++q) g[q] = q < k ? block_sum<kMaxThreads>(lg[q], red) + coef[N + 1 + q] : 0.0;
 }
 
 __global__ void __launch_bounds__(kMaxThreads) argmax_tps_kernel(const double* __restrict__ x,
@@ -388,14 +388,16 @@ __global__ void __launch_bounds__(kMaxThreads) argmax_tps_kernel(const double* _
     }
     __syncthreads();
     const int start = sidx[0];
-    double z[3] = {0, 0, 0}, g[3], f;
+    double z[3] = {0, 0, 0}, g[3] = {0, 0, 0}, f;
     for (int q = 0; q < k; ++q) z[q] = start >= 0 ? X[static_cast<int64_t>(start) * k + q] : 0.5 * (lo[q] + hi[q]);
     f_and_grad(X, C, N, k, z, f, g, red);
     // inverse-Hessian approximation of -f (ascent direction H g)
     double H[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
     double scale = 0.0;
     for (int q = 0; q < k; ++q) scale = fmax(scale, hi[q] - lo[q]);
-    for (int q = 0; q < k; ++q) H[q][q] = 0.1 * scale / fmax(1e-300, sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]));
+    double gn0 = 0.0;
+    for (int q = 0; q < k; ++q) gn0 += g[q] * g[q];
+    for (int q = 0; q < k; ++q) H[q][q] = 0.1 * scale / fmax(1e-300, sqrt(gn0));
     for (int it = 0; it < iters; ++it) {
         double p[3] = {0, 0, 0};
         for (int a = 0; a < k; ++a)

@@ -10,7 +10,15 @@ d p / d theta) the search can follow Monte Carlo gradients directly:
       quantiles q and allocations a, one mc_design_grad launch per step with
       a fixed stream key (common random numbers across steps);
   grid_argmax     -- mc_design_eval over the grid, local-quadratic smoothing,
-      argmax (the grid + smoothing route).
+      argmax (the grid + smoothing route);
+  optimise_alpha  -- the paper's alpha optimisation for one set of nested
+      populations (Sec. 2.1-2.3): N3 splits of the alpha budget, each scaled
+      to the FWER constraint on the device (mc_fwer_calibrate), the expected
+      power of each (Eq. 4, prior folded in) from shared draws, a thin-plate
+      spline over the splits and its maximiser (mc_tps_fit / mc_tps_argmax);
+  optimise_design -- the outer loop over nested populations r (Sec. 2.4):
+      optimise_alpha for every r, a spline of the optimal power over r and
+      its maximiser.
 
 Both return the design parameters; evaluating them exactly is the caller's
 business.  All sampling runs in libmcdesign; this module only loops.
@@ -78,3 +86,96 @@ def grid_argmax(ctx, prob, g1, g2, seed=0, bandwidth=3.0, degree=2):
     idx = int(r["argmax_idx"].item())
     plan.close()
     return idx // g2, idx % g2, float(r["argmax_val"].item())
+
+
+def _dev(a, device):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), dtype=torch.float64, device=device)
+
+
+def optimise_alpha(ctx, cond, r, n3=2000, n_draws=10_000_000, seed=0, smoothing=1e-6, rounds=14,
+                   final_draws=100_000_000, u=None):
+    """Maximise the expected power over the alpha allocations of condition
+    `cond` (workloads.PAPER_EFFECTS) at population fractions r, with the
+    FWER constraint of Eq. 2 (alpha0 = 0.025).
+
+    Points u of the box [0,1]^(n-1) map to splits w (workloads.split_from_box);
+    each split's scale is calibrated on the device under the null
+    (n_draws per round, one stream for all splits), its expected power
+    estimated under the prior-folded alternative (n_draws, one stream for all
+    splits), a thin-plate spline with `smoothing` is fitted over u and
+    maximised in the box, and the split at the maximiser is calibrated once
+    more with final_draws.  Returns dict u, alpha, p_fit (the spline's
+    maximum), p_hat (the point estimates), scale."""
+    import torch
+
+    import workloads
+    r = np.asarray(r, dtype=np.float64)
+    n = r.shape[0]
+    m, C, Sig0 = workloads.paper_law(cond, r)
+    if u is None:
+        u = workloads.box_points(n3, n - 1, seed)
+    w = workloads.split_from_box(u)
+    N3 = w.shape[0]
+    dev = torch.device("cuda", ctx.device)
+    zeros = _dev(np.zeros(N3 * n), dev)
+    null = binding.DeviceProblem([n], np.zeros(N3), np.full(N3, n_draws), np.zeros(N3), _dev(Sig0.ravel(), dev),
+                                 zeros, zeros)
+    cal = binding.mc_fwer_calibrate(ctx, null, _dev(w.ravel(), dev), workloads.ALPHA0, rounds=rounds, seed=seed)
+    alt = binding.DeviceProblem([n], np.zeros(N3), np.full(N3, n_draws), np.ones(N3), _dev(C.ravel(), dev),
+                                _dev(np.tile(m, N3), dev), cal["b"])
+    plan = binding.Plan(ctx, alt, shared=True)
+    p_hat = plan.eval(seed + 1)["p"]
+    x = _dev(u, dev).reshape(1, N3, n - 1)
+    fit = binding.mc_tps_fit(ctx, x, p_hat.reshape(1, N3), smoothing=smoothing)
+    lo, hi = _dev(np.zeros(n - 1), dev), _dev(np.ones(n - 1), dev)
+    am = binding.mc_tps_argmax(ctx, x, fit, lo, hi, iters=300)
+    ctx.sync_status()
+    u_star = am["x"].cpu().numpy()[0]
+    w_star = workloads.split_from_box(u_star)[0]
+    one = binding.DeviceProblem([n], [0], [final_draws], [2], _dev(Sig0.ravel(), dev), _dev(np.zeros(n), dev),
+                                _dev(np.zeros(n), dev))
+    c1 = binding.mc_fwer_calibrate(ctx, one, _dev(w_star, dev), workloads.ALPHA0, rounds=rounds, seed=seed + 2)
+    ctx.sync_status()
+    scale = float(c1["scale"].item())
+    plan.close()
+    return {"u": u_star, "alpha": scale * w_star, "scale": scale, "p_fit": float(am["f"].item()),
+            "p_hat": p_hat.cpu().numpy()}
+
+
+def optimise_design(ctx, cond, r_pairs=None, n3=2000, n_draws=10_000_000, seed=0, smoothing=1e-6,
+                    r_smoothing=1e-6):
+    """The choice of nested populations for n = 3 (Sec. 2.4 with power as
+    the utility): optimise_alpha at every r = (1, r2, r3) of r_pairs
+    (default the paper's 171 pairs), a thin-plate spline of the optimal power
+    over (r2, r3 / r2), its maximiser within two grid steps of the best
+    evaluated pair (the search starts from the best point, as Sec. 2.3 does
+    for alpha; the box stays inside the range of the evaluated pairs, so
+    1 > r2 > r3 > 0 holds and the spline is not extrapolated into regions
+    without data), and optimise_alpha at the maximiser.  Returns dict r,
+    alpha, p_fit, per_r (list of (r2, r3, p_fit))."""
+    import torch
+
+    import workloads
+    pairs = workloads.paper_r_pairs() if r_pairs is None else r_pairs
+    per_r = []
+    for q, (r2, r3) in enumerate(pairs):
+        res = optimise_alpha(ctx, cond, (1.0, r2, r3), n3=n3, n_draws=n_draws, seed=seed + 7 * q,
+                             smoothing=smoothing, final_draws=n_draws)
+        per_r.append((r2, r3, res["p_fit"]))
+    dev = torch.device("cuda", ctx.device)
+    pts = np.array([[a, b / a] for a, b, _ in per_r])
+    vals = np.array([v for _, _, v in per_r])
+    x = _dev(pts, dev).reshape(1, len(per_r), 2)
+    fit = binding.mc_tps_fit(ctx, x, _dev(vals, dev).reshape(1, -1), smoothing=r_smoothing)
+    ib = int(np.argmax(vals))
+    step = float(np.min(np.diff(np.unique(pts[:, 0])))) if len(np.unique(pts[:, 0])) > 1 else 0.05
+    reach = np.array([2.0 * step, 2.0 * step / pts[ib, 0]])
+    lo = _dev(np.maximum(pts.min(0), pts[ib] - reach), dev)
+    hi = _dev(np.minimum(pts.max(0), pts[ib] + reach), dev)
+    am = binding.mc_tps_argmax(ctx, x, fit, lo, hi, iters=300)
+    ctx.sync_status()
+    r2s, v = am["x"].cpu().numpy()[0]
+    r_best = (1.0, float(r2s), float(r2s * v))
+    best = optimise_alpha(ctx, cond, r_best, n3=n3, n_draws=n_draws, seed=seed + 1000, smoothing=smoothing)
+    return {"r": r_best, "alpha": best["alpha"], "p_fit": best["p_fit"], "per_r": per_r}

@@ -463,6 +463,49 @@ def paper_two_layer(cond="c", N1=1024, N2=4096, alphas=None, seed=0, key=0):
                    structures=[{"kind": "dense"}])
 
 
+# Hazard reduction of the biomarker conditions as a function of the
+# population fraction (Sec. 3): Delta_i = intercept + slope r_i, with I3.
+PAPER_EFFECTS = {"a": (0.25, 0.0, 127.0), "b": (0.3, -0.1, 211.0), "c": (0.8, -0.6, 211.0)}
+
+
+def paper_law(cond, r, prior_sd_scale=20.0):
+    """Laws of condition `cond` at population fractions r (r_1 = 1): the
+    Z statistics under the alternative with the prior folded in (mean,
+    covariance; as in paper_design) and under the null, Sigma(r) (Eq. 1)."""
+    icpt, slope, I3v = PAPER_EFFECTS[cond]
+    r = np.asarray(r, dtype=np.float64)
+    m, C, _ = paper_design(r, np.full(r.shape[0], 0.01), I3v, icpt + slope * r, prior_sd_scale)
+    return m, C, nested_sigma(r)
+
+
+def split_from_box(u):
+    """Map points u of the box [0, 1]^(n-1) onto splits w of the alpha
+    budget (the simplex of n weights): w_1 = u_1, w_j = u_j prod_{l<j}(1 - u_l),
+    w_n = prod_l (1 - u_l).  Every split with FWER alpha0 is a ray of the
+    constraint surface of Eq. 2, so the box covers the paper's design space
+    of alpha with its constraint (the alpha scale is solved per split)."""
+    u = np.atleast_2d(np.asarray(u, dtype=np.float64))
+    rest = np.ones(u.shape[0])
+    cols = []
+    for j in range(u.shape[1]):
+        cols.append(rest * u[:, j])
+        rest = rest * (1.0 - u[:, j])
+    cols.append(rest)
+    return np.stack(cols, 1)
+
+
+def box_points(n, k, seed=0):
+    """n uniform points of [0, 1]^k (numpy default_rng(seed))."""
+    return np.random.default_rng(seed).uniform(0.0, 1.0, (n, k))
+
+
+def paper_r_pairs(step=0.05):
+    """The paper's grid of nested populations for n = 3 (Sec. 3: 171 pairs):
+    r = (1, r2, r3) with r2 > r3 on the grid step, 2 step, ..., 1 - step."""
+    g = np.round(np.arange(step, 1.0 - step / 2, step), 10)
+    return [(float(a), float(b)) for i, a in enumerate(g) for b in g[:i]]
+
+
 def paper_alpha_points(cond="c", n=2000, seed=0, total=0.025):
     """n alpha vectors of a condition's dimension for timing one optimisation
     problem of the paper (N3 alpha points, Sec. 3): Dirichlet(1) weights
