@@ -73,7 +73,7 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the d=10/20, smoothing and C3 lines")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle baseline")
-    ap.add_argument("--case", default=None, choices=["c2-small", "c4-small", "c5-small", "smooth"],
+    ap.add_argument("--case", default=None, choices=["c2-small", "c4-small", "c5-small", "smooth", "c2-shared"],
                     help="run a small profiling case (a few launches, no timing) and exit")
     return ap.parse_args()
 
@@ -673,6 +673,18 @@ def run_case(case):
         v = torch.rand(S * G * G, dtype=torch.float64, device="cuda")
         for _ in range(3):
             pkg.mc_smooth_argmax(ctx, v, S, G, G, bandwidth=3.0, degree=2)
+        ctx.sync_status()
+        return
+    if case == "c2-shared":
+        # two scenarios of the d=3 grid (2 x 4096 designs, one stream each), 1e6 draws
+        prob = workloads.c2(n_scen=2, n_draws=1_000_000)
+        dp = pkg.DeviceProblem.from_workload(prob)
+        jac = torch.as_tensor(prob.jac_packed(), dtype=torch.float64, device="cuda")
+        fwd = pkg.Plan(ctx, dp, shared=True)
+        adj = pkg.Plan(ctx, dp, shared=True, grad=True, k=4)
+        for s in range(2):
+            fwd.eval(s)
+            adj.grad(s, jac, 0.01)
         ctx.sync_status()
         return
     if case == "c2-small":

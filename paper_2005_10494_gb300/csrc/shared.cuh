@@ -7,9 +7,10 @@
 // once, with the per-design kernel's Philox / Box-Muller / transform
 // arithmetic, into shared memory; then every thread tests its designs against
 // every draw of the batch (broadcast shared loads).  A design's indicator is
-// the same FP32 comparison as in the per-design kernel, so hit counts are
-// bit-identical to it; the gradient sums differ only in the order of FP32
-// additions.  Draws outside the tile's range enter as y = -inf, z = 0, which
+// the per-design kernel's FP32 comparison y_i > t_i, evaluated as the sign of
+// the FP32 difference t_i - y_i (an exactly equivalent test), so hit counts
+// are bit-identical to it; the gradient sums differ only in the order of
+// FP32 additions.  Draws outside the tile's range enter as y = -inf, z = 0, which
 // no region test counts and which add nothing to any sum.
 //
 // The paper's two-layer estimator (Sec. 2.2, Eq. 7) has this form too: its
@@ -173,10 +174,18 @@ __global__ void __launch_bounds__(kSharedThreads) shared_kernel(const __grid_con
 #pragma unroll
                 for (int q = 0; q < DPT; ++q) {
                     if (q >= nq) break;
-                    bool hit = false;
+                    // y_i > t_i exactly when the FP32 difference t_i - y_i is
+                    // negative: two unequal floats never subtract to zero
+                    // (gradual underflow), rounding keeps the sign, and the
+                    // infinities (dropped tests, draws outside the range)
+                    // give +inf.  So the hit is the sign bit of the or of the
+                    // differences: FADDs and one or per draw instead of a
+                    // compare and a predicate merge per coordinate.
+                    uint32_t sgn = 0u;
 #pragma unroll
-                    for (int i = 0; i < D; ++i) hit |= (y[i] > t[q][i]);
-                    cnt[q] += hit ? 1u : 0u;
+                    for (int i = 0; i < D; ++i) sgn |= __float_as_uint(__fsub_rn(t[q][i], y[i]));
+                    const uint32_t hit = sgn >> 31;
+                    cnt[q] += hit;
                     if constexpr (GRAD) {
                         const float hv = hit ? 1.0f : 0.0f;
 #pragma unroll
