@@ -93,3 +93,23 @@ def argmax(x, c, d, lo, hi, x0=None):
                             method="L-BFGS-B", bounds=list(zip(lo, hi)),
                             options={"ftol": 1e-15, "gtol": 1e-12, "maxiter": 500})
     return res.x, -res.fun
+
+
+def gcv(x, y, s):
+    """Generalised cross-validation score of the smoothing spline,
+    V(s) = N |(I - A_s) y|^2 / tr(I - A_s)^2 with A_s the influence matrix
+    (fitted = A_s y), through the inverse of the full system: the block G
+    with c = G y gives (I - A_s) y = s c and tr(I - A_s) = s tr G."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    N, k = x.shape
+    K = eta(_dist(x, x), k)
+    P = np.hstack([np.ones((N, 1)), x])
+    m = k + 1
+    M = np.zeros((N + m, N + m))
+    M[:N, :N] = K + s * np.eye(N)
+    M[:N, N:] = P
+    M[N:, :N] = P.T
+    G = np.linalg.inv(M)[:N, :N]
+    c = G @ y
+    return N * float((s * c) @ (s * c)) / float(s * np.trace(G)) ** 2

@@ -70,3 +70,33 @@ def test_argmax_of_a_sampled_peak():
     xs, fs = tps.argmax(x, c, d, np.zeros(2), np.ones(2))
     np.testing.assert_allclose(xs, peak, atol=2e-3)
     assert fs == pytest.approx(1.0, abs=1e-3)
+
+
+@pytest.mark.parametrize("k,s", [(1, 1e-3), (2, 0.01), (2, 0.3), (3, 0.05)])
+def test_gcv_matches_the_influence_matrix(k, s):
+    # V(s) = N |(I - A) y|^2 / tr(I - A)^2 with A built column by column from
+    # fits to the unit vectors (A e_j = fitted values of the data e_j)
+    rng = np.random.default_rng(40 + k)
+    N = 40
+    x = rng.uniform(0, 1, (N, k))
+    y = np.sin(4 * x).sum(1) + rng.normal(0, 0.1, N)
+    A = np.empty((N, N))
+    for j in range(N):
+        e = np.zeros(N)
+        e[j] = 1.0
+        c, d = tps.fit(x, e, s)
+        A[:, j] = tps.evaluate(x, x, c, d)
+    r = y - A @ y
+    ref = N * (r @ r) / np.trace(np.eye(N) - A) ** 2
+    assert tps.gcv(x, y, s) == pytest.approx(ref, rel=1e-8)
+
+
+def test_gcv_prefers_smoothing_noisy_data():
+    rng = np.random.default_rng(8)
+    x = rng.uniform(0, 1, (120, 2))
+    y = np.exp(-3 * ((x - 0.5) ** 2).sum(1)) + rng.normal(0, 0.05, 120)
+    grid = np.logspace(-8, 1, 19)
+    scores = [tps.gcv(x, y, s) for s in grid]
+    best = grid[int(np.argmin(scores))]
+    assert 1e-6 < best < 10.0        # neither interpolation nor the plane
+    assert min(scores) < scores[0] and min(scores) < scores[-1]
