@@ -254,6 +254,20 @@ mcd_status mc_fwer_calibrate(mcd_ctx* ctx, const mcd_problem* prob, const double
 mcd_status mc_tps_fit(mcd_ctx* ctx, int32_t n_surf, int32_t n_pts, int32_t k, const double* x,
                       const double* y, double smoothing, double* coef, double* fitted, mcd_stream stream);
 
+/* Generalised cross-validation score of the smoothing spline of one set of
+ * estimates for each of n_s smoothing values: with A_s the influence matrix
+ * (fitted values = A_s y), V(s) = n_pts |(I - A_s) y|^2 / tr(I - A_s)^2.
+ * The smoothing that minimises V is the usual automatic choice for a thin
+ * plate spline (Sec. 2.3 does not state how its spline was tuned).
+ *   x, y: DEVICE as in mc_tps_fit (one surface);  s_values: HOST [n_s],
+ *   each finite and > 0, n_s in 1..256;  score: DEVICE [n_s], NaN where the
+ *   system is singular to working precision at that s.
+ * Per value one FP64 Cholesky and one triangular inverse (tr(I - A_s) is
+ * s |L^{-1}|_F^2); workspace 3 n_pts^2 doubles, in stream order; not for use
+ * under stream capture. */
+mcd_status mc_tps_gcv(mcd_ctx* ctx, int32_t n_pts, int32_t k, const double* x, const double* y,
+                      int32_t n_s, const double* s_values, double* score, mcd_stream stream);
+
 /* Maximise each fitted spline inside the box lo <= x <= hi (DEVICE [k] each,
  * shared by all surfaces), as Sec. 2.3 does with a quasi-Newton method
  * started at the best fitted point: projected BFGS with Armijo backtracking,

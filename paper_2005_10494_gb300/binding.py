@@ -70,6 +70,7 @@ def load(path=LIB_PATH):
         "mc_fwer_calibrate": (i32, [vp, ctypes.POINTER(CProblem), vp, f64, i32, u64, vp, vp, vp, vp]),
         "mc_tps_fit": (i32, [vp, i32, i32, i32, vp, vp, f64, vp, vp, vp]),
         "mc_tps_argmax": (i32, [vp, i32, i32, i32, vp, vp, vp, vp, vp, i32, vp, vp, vp]),
+        "mc_tps_gcv": (i32, [vp, i32, i32, vp, vp, i32, ctypes.POINTER(f64), vp, vp]),
         "mcd_debug_normals": (i32, [vp, u64, u64, u64, u64, vp, vp, vp, vp]),
         "mc_design_eval_noalloc": (i32, [ctypes.c_int, ctypes.POINTER(CProblem), u64, vp, vp, vp, vp]),
     }
@@ -330,6 +331,21 @@ def mc_tps_fit(ctx, x, y, smoothing=0.0, stream=None):
     ctx.check(ctx.lib.mc_tps_fit(ctx.handle, S, N, k, _ptr(x), _ptr(y), float(smoothing), _ptr(coef), _ptr(fitted),
                                  _stream(stream)))
     return {"coef": coef, "fitted": fitted}
+
+
+def mc_tps_gcv(ctx, x, y, s_values, stream=None):
+    """GCV scores of the smoothing spline of one surface (x [n_pts, k],
+    y [n_pts], FP64 CUDA tensors) for each smoothing value (host sequence).
+    Returns an FP64 CUDA tensor [len(s_values)]."""
+    torch = _torch()
+    if x.dim() != 2 or y.dim() != 1 or x.shape[0] != y.shape[0]:
+        raise ValueError("x must be [n_pts, k] and y [n_pts]")
+    N, k = (int(v) for v in x.shape)
+    sv = np.ascontiguousarray(s_values, dtype=np.float64)
+    score = torch.empty(len(sv), dtype=torch.float64, device=x.device)
+    ctx.check(ctx.lib.mc_tps_gcv(ctx.handle, N, k, _ptr(x.contiguous()), _ptr(y.contiguous()), len(sv),
+                                 sv.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(score), _stream(stream)))
+    return score
 
 
 def mc_tps_argmax(ctx, x, fit, lo, hi, iters=200, stream=None):

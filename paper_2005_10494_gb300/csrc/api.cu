@@ -1039,6 +1039,35 @@ mcd_status mc_tps_fit(mcd_ctx* ctx, int32_t n_surf, int32_t n_pts, int32_t k, co
     return rc;
 }
 
+mcd_status mc_tps_gcv(mcd_ctx* ctx, int32_t n_pts, int32_t k, const double* x, const double* y, int32_t n_s,
+                      const double* s_values, double* score, mcd_stream stream) {
+    if (!ctx) return MCD_EINVAL;
+    if (k < 1 || k > 3) return fail(ctx, MCD_EINVAL, "k must be 1, 2 or 3");
+    if (n_pts < k + 2 || n_pts > 16384) return fail(ctx, MCD_EINVAL, "n_pts must be in k + 2 .. 16384");
+    if (n_s < 1 || n_s > 256 || !s_values) return fail(ctx, MCD_EINVAL, "n_s must be in 1..256 with s_values given");
+    for (int q = 0; q < n_s; ++q)
+        if (!(s_values[q] > 0.0) || s_values[q] == INFINITY)
+            return fail(ctx, MCD_EINVAL, "smoothing values must be finite and > 0", q);
+    if (!x || !y || !score) return fail(ctx, MCD_EINVAL, "x, y and score must not be NULL");
+    if (!is_device_ptr(x) || !is_device_ptr(y) || !is_device_ptr(score))
+        return fail(ctx, MCD_EINVAL, "x, y and score must be device memory");
+    MCD_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    MCD_CUDA(cudaStreamIsCapturing(s, &cs), "cudaStreamIsCapturing");
+    if (cs != cudaStreamCaptureStatusNone) return fail(ctx, MCD_EINVAL, "mc_tps_gcv cannot be captured");
+    const size_t nws = tps_gcv_workspace_doubles(n_pts, k);
+    double* ws = nullptr;
+    MCD_CUDA(cudaMallocAsync(&ws, sizeof(double) * (nws + 4), s), "spline workspace");
+    int* bad = reinterpret_cast<int*>(ws + nws);
+    unsigned long long* amax = reinterpret_cast<unsigned long long*>(ws + nws + 1);
+    double* trace = ws + nws + 2;
+    cudaError_t e = tps_gcv(x, y, n_pts, k, s_values, n_s, score, ws, bad, amax, trace, s);
+    cudaFreeAsync(ws, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "spline GCV launch");
+    return MCD_OK;
+}
+
 mcd_status mc_tps_argmax(mcd_ctx* ctx, int32_t n_surf, int32_t n_pts, int32_t k, const double* x, const double* coef,
                          const double* fitted, const double* lo, const double* hi, int32_t iters, double* x_best,
                          double* f_best, mcd_stream stream) {

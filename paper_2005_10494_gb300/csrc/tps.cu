@@ -327,6 +327,107 @@ __global__ void __launch_bounds__(1024) combine_kernel(const double* __restrict_
         for (int i = threadIdx.x; i < N; i += blockDim.x) fitted[i] = y[i] - s * coef[i];
 }
 
+// ---- generalised cross-validation ------------------------------------------
+// With T = Q2^T K Q2 (the projection at s = 0) and M = T + s I = L L^T,
+// (I - A_s) y = s c with |c| = |w|, w = M^{-1} y~_2, and tr(I - A_s) =
+// s tr(M^{-1}) = s |L^{-1}|_F^2, so V(s) = N |w|^2 / |L^{-1}|_F^4.
+
+// dst (n x n, leading dimension n) = src (leading dimension lds) + s I,
+// lower triangle and diagonal.
+__global__ void shift_copy_kernel(const double* __restrict__ src, int64_t lds, double* __restrict__ dst, int n,
+                                  double s) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (j > i || i >= n) return;
+    dst[static_cast<int64_t>(i) * n + j] = src[static_cast<int64_t>(i) * lds + j] + (i == j ? s : 0.0);
+}
+
+// Inverse of each b x b lower-triangular diagonal block of L (leading
+// dimension n), into the same block of X; thread c makes column c.
+__global__ void __launch_bounds__(kNb) tri_inv_diag_kernel(const double* __restrict__ L, double* __restrict__ X,
+                                                          int n) {
+    __shared__ double a[kNb][kNb + 1];
+    __shared__ double x[kNb][kNb + 1];
+    const int j0 = blockIdx.x * kNb;
+    const int b = n - j0 < kNb ? n - j0 : kNb;
+    const int c = threadIdx.x;
+    for (int r = 0; r < kNb; ++r) a[r][c] = (r < b && c <= r) ? L[static_cast<int64_t>(j0 + r) * n + j0 + c] : 0.0;
+    __syncthreads();
+    if (c < b) {
+        for (int r = 0; r < kNb; ++r) x[r][c] = 0.0;
+        x[c][c] = 1.0 / a[c][c];
+        for (int r = c + 1; r < b; ++r) {
+            double t = 0.0;
+            for (int l = c; l < r; ++l) t += a[r][l] * x[l][c];
+            x[r][c] = -t / a[r][r];
+        }
+        for (int r = c; r < b; ++r) X[static_cast<int64_t>(j0 + r) * n + j0 + c] = x[r][c];
+    }
+}
+
+// Block row i of X = L^{-1} (i >= 1): for every block column j < i,
+// X_ij = -X_ii (sum_{l=j}^{i-1} L_il X_lj), 32 x 32 blocks, one block per j.
+__global__ void __launch_bounds__(256) tri_inv_step_kernel(const double* __restrict__ L, double* __restrict__ X,
+                                                           int n, int bi) {
+    __shared__ double ls[kNb][kNb + 1];
+    __shared__ double xs[kNb][kNb + 1];
+    const int bj = blockIdx.x;
+    const int i0 = bi * kNb, j0 = bj * kNb;
+    const int tr = threadIdx.x / 8, tc0 = (threadIdx.x % 8) * 4;      // row tr, columns tc0 .. tc0 + 3
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int bl = bj; bl < bi; ++bl) {
+        const int l0 = bl * kNb;
+        for (int t = threadIdx.x; t < kNb * kNb; t += blockDim.x) {
+            const int r = t / kNb, q = t % kNb;
+            ls[r][q] = (i0 + r < n) ? L[static_cast<int64_t>(i0 + r) * n + l0 + q] : 0.0;
+            xs[r][q] = (l0 + r >= j0 + q) ? X[static_cast<int64_t>(l0 + r) * n + j0 + q] : 0.0;   // lower part only
+        }
+        __syncthreads();
+        for (int l = 0; l < kNb; ++l) {
+            const double lv = ls[tr][l];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = fma(lv, xs[l][tc0 + q], acc[q]);
+        }
+        __syncthreads();
+    }
+    // X_ij = -X_ii S: S through shared memory, X_ii from X
+    for (int q = 0; q < 4; ++q) xs[tr][tc0 + q] = acc[q];
+    for (int t = threadIdx.x; t < kNb * kNb; t += blockDim.x) {
+        const int r = t / kNb, q = t % kNb;
+        ls[r][q] = (i0 + r < n && i0 + q < n && q <= r) ? X[static_cast<int64_t>(i0 + r) * n + i0 + q] : 0.0;
+    }
+    __syncthreads();
+    if (i0 + tr < n) {
+        for (int q = 0; q < 4; ++q) {
+            double v = 0.0;
+            for (int l = 0; l <= tr; ++l) v += ls[tr][l] * xs[l][tc0 + q];
+            X[static_cast<int64_t>(i0 + tr) * n + j0 + tc0 + q] = -v;
+        }
+    }
+}
+
+// |X|_F^2 over the lower triangle (n x n, leading dimension n).
+__global__ void sumsq_lower_kernel(const double* __restrict__ X, int n, double* __restrict__ out) {
+    const int i = blockIdx.x;
+    double s = 0.0;
+    for (int j = threadIdx.x; j <= i; j += blockDim.x) {
+        const double v = X[static_cast<int64_t>(i) * n + j];
+        s += v * v;
+    }
+    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+// V(s) = N |w|^2 / tr^2, NaN when the factorisation failed.
+__global__ void __launch_bounds__(1024) gcv_score_kernel(const double* __restrict__ w, int n, const double* __restrict__ tr,
+                                                         const int* __restrict__ bad, int N, double* __restrict__ out) {
+    __shared__ double red[32];
+    double l = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) l += w[i] * w[i];
+    const double ww = block_sum<1024>(l, red);
+    if (threadIdx.x == 0) *out = *bad ? NAN : static_cast<double>(N) * ww / (*tr * *tr);
+}
+
 // ---- maximiser ---------------------------------------------------------------
 constexpr int kMaxThreads = 256;
 
@@ -455,6 +556,23 @@ __global__ void __launch_bounds__(kMaxThreads) argmax_tps_kernel(const double* _
 
 }  // namespace
 
+// Blocked Cholesky (lower, in place) of the n x n matrix at B (leading
+// dimension ld).
+static void chol_blocked(double* B, int64_t ld, int n, const unsigned long long* amax, int* bad, cudaStream_t stream) {
+    for (int j0 = 0; j0 < n; j0 += kNb) {
+        const int b = n - j0 < kNb ? n - j0 : kNb;
+        double* G = B + j0 * ld + j0;
+        chol_diag_kernel<<<1, kNb * kNb, 0, stream>>>(G, ld, b, n, amax, bad);
+        const int rem = n - j0 - b;
+        if (rem > 0) {
+            double* Pn = G + b * ld;
+            chol_trsm_kernel<<<(rem + 127) / 128, 128, 0, stream>>>(G, Pn, ld, b, rem);
+            const int tiles = (rem + kSyrkTile - 1) / kSyrkTile;
+            chol_syrk_kernel<<<dim3(tiles, tiles), 256, 0, stream>>>(Pn + b, Pn, ld, b, rem);
+        }
+    }
+}
+
 size_t tps_workspace_doubles(int N, int k) {
     const size_t m = static_cast<size_t>(k) + 1;
     return static_cast<size_t>(N) * N + 2 * m * N + 3 * static_cast<size_t>(N) + m * m + m + 8;
@@ -488,23 +606,64 @@ cudaError_t tps_fit_one(const double* x, const double* y, int N, int k, double s
     const int n = N - m;
     double* B = A + static_cast<size_t>(m) * N + m;
     maxabs_kernel<<<256, 256, 0, stream>>>(A, static_cast<int64_t>(N) * N, amax);
-    for (int j0 = 0; j0 < n; j0 += kNb) {
-        const int b = n - j0 < kNb ? n - j0 : kNb;
-        double* G = B + static_cast<size_t>(j0) * N + j0;
-        chol_diag_kernel<<<1, kNb * kNb, 0, stream>>>(G, N, b, n, amax, bad);
-        const int rem = n - j0 - b;
-        if (rem > 0) {
-            double* Pn = G + static_cast<size_t>(b) * N;
-            chol_trsm_kernel<<<(rem + 127) / 128, 128, 0, stream>>>(G, Pn, N, b, rem);
-            const int tiles = (rem + kSyrkTile - 1) / kSyrkTile;
-            chol_syrk_kernel<<<dim3(tiles, tiles), 256, 0, stream>>>(Pn + b, Pn, N, b, rem);
-        }
-    }
+    chol_blocked(B, N, n, amax, bad, stream);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(z, yt + m, sizeof(double) * n, cudaMemcpyDeviceToDevice, stream)) != cudaSuccess) return e;
     chol_solve_kernel<<<1, kSolveThreads, 0, stream>>>(B, N, n, z);
     combine_kernel<<<1, 1024, 0, stream>>>(A, V, tau, R, yt, z, y, N, k, s, bad, coef, fitted, status, surf);
     return cudaGetLastError();
+}
+
+size_t tps_gcv_workspace_doubles(int N, int k) {
+    const size_t n = static_cast<size_t>(N) - (k + 1);
+    return tps_workspace_doubles(N, k) + 2 * n * n + 8;
+}
+
+cudaError_t tps_gcv(const double* x, const double* y, int N, int k, const double* s_values, int n_s, double* score,
+                    double* ws, int* bad, unsigned long long* amax, double* trace, cudaStream_t stream) {
+    const int m = k + 1;
+    const int n = N - m;
+    double* A = ws;
+    double* V = A + static_cast<size_t>(N) * N;
+    double* Pw = V + static_cast<size_t>(m) * N;
+    double* yt = Pw + static_cast<size_t>(m) * N;
+    double* w = yt + N;
+    double* z = w + N;
+    double* R = z + N;
+    double* tau = R + m * m;
+    double* W = ws + tps_workspace_doubles(N, k);
+    double* X = W + static_cast<size_t>(n) * n;
+    // projection of K (s = 0) and y~
+    assemble_kernel<<<dim3((N + 255) / 256, N), 256, 0, stream>>>(A, x, N, k, 0.0);
+    qr_kernel<<<1, kQrThreads, 0, stream>>>(x, y, N, k, Pw, V, tau, R, yt);
+    for (int j = 0; j < m; ++j) {
+        const double* v = V + static_cast<size_t>(j) * N;
+        matvec_kernel<<<(N + 7) / 8, 256, 0, stream>>>(A, v, w, N);
+        rank2_prep_kernel<<<1, 1024, 0, stream>>>(v, w, tau, j, N);
+        rank2_kernel<<<dim3((N + 255) / 256, N), 256, 0, stream>>>(A, v, w, N);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const double* T22 = A + static_cast<size_t>(m) * N + m;
+    const int nb = (n + kNb - 1) / kNb;
+    for (int q = 0; q < n_s; ++q) {
+        if ((e = cudaMemsetAsync(bad, 0, sizeof(int), stream)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(amax, 0, sizeof(unsigned long long), stream)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(trace, 0, sizeof(double), stream)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(X, 0, sizeof(double) * static_cast<size_t>(n) * n, stream)) != cudaSuccess) return e;
+        shift_copy_kernel<<<dim3((n + 255) / 256, n), 256, 0, stream>>>(T22, N, W, n, s_values[q]);
+        maxabs_kernel<<<256, 256, 0, stream>>>(W, static_cast<int64_t>(n) * n, amax);
+        chol_blocked(W, n, n, amax, bad, stream);
+        if ((e = cudaMemcpyAsync(z, yt + m, sizeof(double) * n, cudaMemcpyDeviceToDevice, stream)) != cudaSuccess)
+            return e;
+        chol_solve_kernel<<<1, kSolveThreads, 0, stream>>>(W, n, n, z);
+        tri_inv_diag_kernel<<<nb, kNb, 0, stream>>>(W, X, n);
+        for (int bi = 1; bi < nb; ++bi) tri_inv_step_kernel<<<bi, 256, 0, stream>>>(W, X, n, bi);
+        sumsq_lower_kernel<<<n, 128, 0, stream>>>(X, n, trace);
+        gcv_score_kernel<<<1, 1024, 0, stream>>>(z, n, trace, bad, N, score + q);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t tps_argmax(const double* x, const double* coef, const double* fitted, int n_surf, int N, int k,

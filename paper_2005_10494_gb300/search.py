@@ -103,10 +103,11 @@ def optimise_alpha(ctx, cond, r, n3=2000, n_draws=10_000_000, seed=0, smoothing=
     each split's scale is calibrated on the device under the null
     (n_draws per round, one stream for all splits), its expected power
     estimated under the prior-folded alternative (n_draws, one stream for all
-    splits), a thin-plate spline with `smoothing` is fitted over u and
+    splits), a thin-plate spline with `smoothing` (a value, or "gcv": the
+    minimiser of the GCV score over 1e-10 .. 1e-2) is fitted over u and
     maximised in the box, and the split at the maximiser is calibrated once
     more with final_draws.  Returns dict u, alpha, p_fit (the spline's
-    maximum), p_hat (the point estimates), scale."""
+    maximum), p_hat (the point estimates), scale, smoothing."""
     import torch
 
     import workloads
@@ -127,6 +128,10 @@ def optimise_alpha(ctx, cond, r, n3=2000, n_draws=10_000_000, seed=0, smoothing=
     plan = binding.Plan(ctx, alt, shared=True)
     p_hat = plan.eval(seed + 1)["p"]
     x = _dev(u, dev).reshape(1, N3, n - 1)
+    if isinstance(smoothing, str):
+        grid = np.logspace(-10, -2, 17)
+        score = binding.mc_tps_gcv(ctx, x[0], p_hat, grid).cpu().numpy()
+        smoothing = float(grid[int(np.nanargmin(score))])
     fit = binding.mc_tps_fit(ctx, x, p_hat.reshape(1, N3), smoothing=smoothing)
     lo, hi = _dev(np.zeros(n - 1), dev), _dev(np.ones(n - 1), dev)
     am = binding.mc_tps_argmax(ctx, x, fit, lo, hi, iters=300)
@@ -140,7 +145,7 @@ def optimise_alpha(ctx, cond, r, n3=2000, n_draws=10_000_000, seed=0, smoothing=
     scale = float(c1["scale"].item())
     plan.close()
     return {"u": u_star, "alpha": scale * w_star, "scale": scale, "p_fit": float(am["f"].item()),
-            "p_hat": p_hat.cpu().numpy()}
+            "p_hat": p_hat.cpu().numpy(), "smoothing": smoothing}
 
 
 def optimise_design(ctx, cond, r_pairs=None, n3=2000, n_draws=10_000_000, seed=0, smoothing=1e-6,

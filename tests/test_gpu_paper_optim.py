@@ -53,3 +53,11 @@ def test_choice_of_nested_populations(ctx):
     # about as good as the paper's design, which the grid does not contain
     assert p >= exact_power("c", PAPER_R_C, PAPER_ALPHA_C) - 1e-3, (r, out["alpha"], p)
     assert abs(r[1] - PAPER_R_C[1]) <= 0.15 and abs(r[2] - PAPER_R_C[2]) <= 0.15, r
+
+
+def test_alpha_optimisation_with_gcv_smoothing(ctx):
+    from paper_2005_10494_gb300 import search
+    res = search.optimise_alpha(ctx, "c", PAPER_R_C, n3=1000, n_draws=4_000_000, seed=1, smoothing="gcv")
+    assert 1e-10 <= res["smoothing"] <= 1e-2
+    p_star = exact_power("c", PAPER_R_C, res["alpha"])
+    assert p_star >= exact_power("c", PAPER_R_C, PAPER_ALPHA_C) - 2e-4, (res["alpha"], p_star, res["smoothing"])

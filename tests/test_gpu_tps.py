@@ -149,3 +149,33 @@ def test_repeated_points_and_bad_arguments(ctx):
     with pytest.raises(pkg.MCDError) as e:
         pkg.mc_tps_fit(ctx, xt[:, :3], yt[:, :3])            # n_pts < k + 2
     assert e.value.code == MCD_EINVAL
+
+
+@pytest.mark.parametrize("k,n,lo", [(2, 300, -6), (1, 97, -4), (3, 130, -5), (2, 65, -6)])
+def test_gcv_matches_oracle(ctx, k, n, lo):
+    import torch
+
+    import paper_2005_10494_gb300 as pkg
+    rng = np.random.default_rng(70 + k + n)
+    x, y = data(rng, n, k)
+    s_values = np.logspace(lo, 0.5, 7)
+    xt = torch.as_tensor(x, dtype=torch.float64, device="cuda")
+    yt = torch.as_tensor(y, dtype=torch.float64, device="cuda")
+    gpu = pkg.mc_tps_gcv(ctx, xt, yt, s_values).cpu().numpy()
+    ctx.sync_status()
+    ref = np.array([tps.gcv(x, y, s) for s in s_values])
+    np.testing.assert_allclose(gpu, ref, rtol=1e-7)
+    assert int(np.argmin(gpu)) == int(np.argmin(ref))
+
+
+def test_gcv_rejects_bad_values(ctx):
+    import torch
+
+    import paper_2005_10494_gb300 as pkg
+    from paper_2005_10494_gb300.binding import MCD_EINVAL
+    x = torch.rand(50, 2, dtype=torch.float64, device="cuda")
+    y = torch.rand(50, dtype=torch.float64, device="cuda")
+    for bad in ([0.0], [1.0, -1.0], [float("inf")], []):
+        with pytest.raises(pkg.MCDError) as e:
+            pkg.mc_tps_gcv(ctx, x, y, bad)
+        assert e.value.code == MCD_EINVAL
