@@ -252,26 +252,62 @@ __global__ void __launch_bounds__(256) chol_syrk_kernel(double* __restrict__ T, 
         }
 }
 
-// Solve L z = r (forward, row-oriented) then L^T w = z (backward,
-// column updates by rows of L), in one block; n x n lower factor at L.
+// Solve L z = r then L^T w = z in place, n x n lower factor at L (leading
+// dimension ld), one block of 32 warps, 32 rows at a time.  Forward: warp r
+// forms row r's product with the solved entries (rows of L read
+// contiguously), then warp 0 solves the 32 x 32 diagonal block with
+// shuffles.  Backward: warp 0 solves the transposed diagonal block, then all
+// threads subtract the block's contribution from the earlier entries
+// (again reading rows of L).
 constexpr int kSolveThreads = 1024;
 __global__ void __launch_bounds__(kSolveThreads) chol_solve_kernel(const double* __restrict__ L, int64_t ld, int n,
                                                                   double* __restrict__ z) {
-    __shared__ double red[kSolveThreads / 32];
-    for (int i = 0; i < n; ++i) {
-        const double* row = L + static_cast<int64_t>(i) * ld;
-        double s = 0.0;
-        for (int j = threadIdx.x; j < i; j += blockDim.x) s += row[j] * z[j];
-        const double tot = block_sum<kSolveThreads>(s, red);
-        if (threadIdx.x == 0) z[i] = (z[i] - tot) / row[i];
+    __shared__ double part[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i0 = 0; i0 < n; i0 += 32) {
+        const int b = n - i0 < 32 ? n - i0 : 32;
+        if (warp < b) {
+            const double* row = L + static_cast<int64_t>(i0 + warp) * ld;
+            double s = 0.0;
+            for (int j = lane; j < i0; j += 32) s += row[j] * z[j];
+            for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) part[warp] = z[i0 + warp] - s;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            double zc = 0.0;                                   // lane c holds z[i0 + c] once solved
+            for (int r = 0; r < b; ++r) {
+                const double lrc = lane < r ? L[static_cast<int64_t>(i0 + r) * ld + i0 + lane] : 0.0;
+                double t = lrc * zc;
+                for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+                const double zr = (part[r] - t) / L[static_cast<int64_t>(i0 + r) * ld + i0 + r];
+                if (lane == r) zc = zr;
+            }
+            if (lane < b) z[i0 + lane] = zc;
+        }
         __syncthreads();
     }
-    for (int j = n - 1; j >= 0; --j) {
-        const double* row = L + static_cast<int64_t>(j) * ld;
-        if (threadIdx.x == 0) z[j] /= row[j];
+    const int nblk = (n + 31) / 32;
+    for (int bi = nblk - 1; bi >= 0; --bi) {
+        const int i0 = bi * 32;
+        const int b = n - i0 < 32 ? n - i0 : 32;
+        if (warp == 0) {
+            double wc = 0.0;                                   // lane c holds w[i0 + c] once solved
+            for (int r = b - 1; r >= 0; --r) {
+                const double lcr = (lane > r && lane < b) ? L[static_cast<int64_t>(i0 + lane) * ld + i0 + r] : 0.0;
+                double t = lcr * wc;
+                for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+                const double wr = (z[i0 + r] - t) / L[static_cast<int64_t>(i0 + r) * ld + i0 + r];
+                if (lane == r) wc = wr;
+            }
+            if (lane < b) z[i0 + lane] = wc;
+        }
         __syncthreads();
-        const double wj = z[j];
-        for (int i = threadIdx.x; i < j; i += blockDim.x) z[i] -= row[i] * wj;
+        for (int j = threadIdx.x; j < i0; j += blockDim.x) {
+            double s = 0.0;
+            for (int r = 0; r < b; ++r) s += L[static_cast<int64_t>(i0 + r) * ld + j] * z[i0 + r];
+            z[j] -= s;
+        }
         __syncthreads();
     }
 }
