@@ -12,6 +12,8 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "fwer.cuh"
 #include "tps.cuh"
 #include "mcd_internal.cuh"
@@ -131,6 +133,15 @@ struct mcd_plan {
 };
 
 namespace {
+
+// NVTX range around one entry point (a no-op unless a profiler is attached),
+// so that traces show planning, launches, calibration and smoothing apart.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 mcd_status fail(mcd_ctx* ctx, mcd_status code, const std::string& msg, int64_t index = -1) {
     if (ctx) {
@@ -794,6 +805,7 @@ mcd_status mcd_sync_status(mcd_ctx* ctx, mcd_stream stream) {
 }
 
 mcd_status mcd_plan_create(mcd_ctx* ctx, const mcd_problem* prob, int32_t flags, int32_t k, mcd_plan** plan) {
+    NvtxRange nvtx_("mcd_plan_create");
     if (!ctx || !plan) return fail(ctx, MCD_EINVAL, "ctx and plan must not be NULL");
     *plan = nullptr;
     if (flags & ~(MCD_PLAN_GRAD | MCD_PLAN_AUTOTUNE | MCD_PLAN_GRAPH | MCD_PLAN_FP64 | MCD_PLAN_TIMING |
@@ -831,6 +843,7 @@ void mcd_plan_destroy(mcd_plan* plan) {
 }
 
 mcd_status mcd_plan_eval(mcd_plan* plan, uint64_t seed, uint64_t* hits, double* p, double* se, mcd_stream stream) {
+    NvtxRange nvtx_("mcd_plan_eval");
     if (!plan) return MCD_EINVAL;
     LaunchArgs a;
     a.seed = seed;
@@ -842,6 +855,7 @@ mcd_status mcd_plan_eval(mcd_plan* plan, uint64_t seed, uint64_t* hits, double* 
 
 mcd_status mcd_plan_grad(mcd_plan* plan, uint64_t seed, const double* dt_dtheta, double h_sigmoid, uint64_t* hits,
                          double* p, double* grad_lr, double* grad_sig, double* grad_se, mcd_stream stream) {
+    NvtxRange nvtx_("mcd_plan_grad");
     if (!plan) return MCD_EINVAL;
     mcd_ctx* ctx = plan->ctx;
     if (!(plan->flags & MCD_PLAN_GRAD)) return fail(ctx, MCD_EINVAL, "plan was created without MCD_PLAN_GRAD");
@@ -894,6 +908,7 @@ mcd_status mcd_plan_kernel_ms(mcd_plan* plan, float* ms) {
 
 static mcd_status one_shot(mcd_ctx* ctx, const mcd_problem* prob, int32_t k, bool grad, const LaunchArgs& a,
                            mcd_stream stream) {
+    NvtxRange nvtx_("mc_design_eval/grad");
     if (!ctx) return MCD_EINVAL;
     mcd_status st = validate_problem(ctx, prob, k);
     if (st != MCD_OK) return st;
@@ -943,6 +958,7 @@ mcd_status mc_design_grad(mcd_ctx* ctx, const mcd_problem* prob, uint64_t seed, 
 
 mcd_status mc_fwer_calibrate(mcd_ctx* ctx, const mcd_problem* prob, const double* w, double alpha0, int32_t rounds,
                              uint64_t seed, double* scale, double* b, double* fwer, mcd_stream stream) {
+    NvtxRange nvtx_("mc_fwer_calibrate");
     if (!ctx) return MCD_EINVAL;
     if (!prob) return fail(ctx, MCD_EINVAL, "problem is NULL");
     if (!(alpha0 > 0.0 && alpha0 < 1.0)) return fail(ctx, MCD_EINVAL, "alpha0 must be in (0, 1)");
@@ -1008,6 +1024,7 @@ mcd_status mc_fwer_calibrate(mcd_ctx* ctx, const mcd_problem* prob, const double
 
 mcd_status mc_tps_fit(mcd_ctx* ctx, int32_t n_surf, int32_t n_pts, int32_t k, const double* x, const double* y,
                       double smoothing, double* coef, double* fitted, mcd_stream stream) {
+    NvtxRange nvtx_("mc_tps_fit");
     if (!ctx) return MCD_EINVAL;
     if (n_surf < 1) return fail(ctx, MCD_EINVAL, "n_surf must be >= 1");
     if (k < 1 || k > 3) return fail(ctx, MCD_EINVAL, "k must be 1, 2 or 3");
@@ -1041,6 +1058,7 @@ mcd_status mc_tps_fit(mcd_ctx* ctx, int32_t n_surf, int32_t n_pts, int32_t k, co
 
 mcd_status mc_tps_gcv(mcd_ctx* ctx, int32_t n_pts, int32_t k, const double* x, const double* y, int32_t n_s,
                       const double* s_values, double* score, mcd_stream stream) {
+    NvtxRange nvtx_("mc_tps_gcv");
     if (!ctx) return MCD_EINVAL;
     if (k < 1 || k > 3) return fail(ctx, MCD_EINVAL, "k must be 1, 2 or 3");
     if (n_pts < k + 2 || n_pts > 16384) return fail(ctx, MCD_EINVAL, "n_pts must be in k + 2 .. 16384");
@@ -1071,6 +1089,7 @@ mcd_status mc_tps_gcv(mcd_ctx* ctx, int32_t n_pts, int32_t k, const double* x, c
 mcd_status mc_tps_argmax(mcd_ctx* ctx, int32_t n_surf, int32_t n_pts, int32_t k, const double* x, const double* coef,
                          const double* fitted, const double* lo, const double* hi, int32_t iters, double* x_best,
                          double* f_best, mcd_stream stream) {
+    NvtxRange nvtx_("mc_tps_argmax");
     if (!ctx) return MCD_EINVAL;
     if (n_surf < 1) return fail(ctx, MCD_EINVAL, "n_surf must be >= 1");
     if (k < 1 || k > 3) return fail(ctx, MCD_EINVAL, "k must be 1, 2 or 3");
@@ -1090,6 +1109,7 @@ mcd_status mc_tps_argmax(mcd_ctx* ctx, int32_t n_surf, int32_t n_pts, int32_t k,
 mcd_status mc_smooth_argmax(mcd_ctx* ctx, int32_t n_scen, int32_t g1, int32_t g2, const double* value,
                             double bandwidth, int32_t degree, double* smoothed, int64_t* argmax_idx,
                             double* argmax_val, int64_t* raw_idx, double* raw_val, mcd_stream stream) {
+    NvtxRange nvtx_("mc_smooth_argmax");
     if (!ctx) return MCD_EINVAL;
     if (n_scen < 1 || g1 < 1 || g2 < 1) return fail(ctx, MCD_EINVAL, "n_scen, g1, g2 must be >= 1");
     if (static_cast<int64_t>(g1) * g2 >= (1ll << 31)) return fail(ctx, MCD_EINVAL, "grid too large");
