@@ -45,14 +45,30 @@ def oracle_same_stream(prob, seed, idx, eps=EPS32, grad=False, h=0.0):
     return mc.mc_batch(oracle_designs(prob, idx), seed, eps=eps, grad=grad, h=h)
 
 
+def report(name, **stats):
+    """Append one JSON line of parity statistics to the file named by the
+    environment variable MCD_PARITY_REPORT (nothing when it is unset)."""
+    import json
+    import os
+    path = os.environ.get("MCD_PARITY_REPORT")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps(dict(check=name, **stats)) + "\n")
+
+
 def assert_discordance(gpu_hits, ora, idx):
-    """|hits_gpu - hits_oracle| <= ambiguous draws, design by design."""
+    """|hits_gpu - hits_oracle| <= ambiguous draws, design by design.
+    Returns (designs, total |difference|, total ambiguous draws)."""
     bad = []
+    tot_diff = tot_amb = 0
     for k, j in enumerate(idx):
         diff = abs(int(gpu_hits[j]) - int(ora["hits"][k]))
+        tot_diff += diff
+        tot_amb += int(ora["ambiguous"][k])
         if diff > int(ora["ambiguous"][k]):
             bad.append((j, int(gpu_hits[j]), int(ora["hits"][k]), int(ora["ambiguous"][k])))
     assert not bad, "designs outside the same-stream band: %r" % bad[:10]
+    return {"designs": len(idx), "hit_difference": tot_diff, "ambiguous_draws": tot_amb}
 
 
 def band(p_exact, n):
@@ -60,6 +76,14 @@ def band(p_exact, n):
 
 
 def assert_band(p_gpu, p_exact, n, idx):
+    """|p_gpu - p_exact| <= 5 SE + 1e-7 per design.  Returns (designs, the
+    largest and the mean |error| in units of SE)."""
     bad = [(j, float(p_gpu[j]), float(p_exact[k])) for k, j in enumerate(idx)
            if abs(p_gpu[j] - p_exact[k]) > band(p_exact[k], n if np.isscalar(n) else n[k])]
     assert not bad, "designs outside 5 SE of the exact value: %r" % bad[:10]
+    z = []
+    for k, j in enumerate(idx):
+        nn = n if np.isscalar(n) else n[k]
+        se = math.sqrt(max(p_exact[k] * (1.0 - p_exact[k]), 1e-300) / nn)
+        z.append(abs(float(p_gpu[j]) - float(p_exact[k])) / se)
+    return {"designs": len(idx), "max_abs_z": max(z) if z else 0.0, "mean_abs_z": float(np.mean(z)) if z else 0.0}

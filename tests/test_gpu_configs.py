@@ -6,7 +6,7 @@ import pytest
 import workloads
 from oracle import design, quad
 
-from gpu_util import EPS64, assert_band, assert_discordance, oracle_same_stream, run
+from gpu_util import EPS64, assert_band, assert_discordance, oracle_same_stream, report, run
 
 pytestmark = pytest.mark.gpu
 
@@ -31,7 +31,7 @@ def test_c2_full_same_stream_sample(c2_full):
     prob, out = c2_full
     idx = sorted(np.random.default_rng(0).choice(prob.n_design, 48, replace=False).tolist())
     ora = oracle_same_stream(prob, 0, idx)
-    assert_discordance(out["hits"], ora, idx)
+    report("c2 same stream (48 designs x 1e6 draws)", **assert_discordance(out["hits"], ora, idx))
 
 
 def test_c2_full_exact_band_sample(c2_full):
@@ -39,7 +39,7 @@ def test_c2_full_exact_band_sample(c2_full):
     idx = sorted(np.random.default_rng(1).choice(prob.n_design, 400, replace=False).tolist())
     sc = workloads.c2_scenarios(16)
     exact = [1.0 - quad.orthant_equi(prob.t(j), sc[prob.design_scen[j]][2]) for j in idx]
-    assert_band(out["p"], exact, 1_000_000, idx)
+    report("c2 vs quadrature (400 designs x 1e6 draws)", **assert_band(out["p"], exact, 1_000_000, idx))
 
 
 def test_c2_full_gradients_vs_fd(c2_full):
@@ -83,7 +83,7 @@ def test_c4_full_exact_sample(ctx):
     out = run(ctx, prob, seed=0, grad=True, k=4, jac=prob.jac_packed(), h=0.01)
     idx = sorted(np.random.default_rng(3).choice(prob.n_design, 24, replace=False).tolist())
     exact = [1.0 - quad.orthant_ar1(prob.t(j), 0.3) for j in idx]
-    assert_band(out["p"], exact, 10_000_000, idx)
+    report("c4 vs AR(1) quadrature (24 designs x 1e7 draws)", **assert_band(out["p"], exact, 10_000_000, idx))
 
 
 def test_c5_full_fp32_and_fp64_vs_exact(ctx):
@@ -92,18 +92,20 @@ def test_c5_full_fp32_and_fp64_vs_exact(ctx):
     idx = workloads.c5_subsample().tolist()
     st = prob.structures[0]
     exact = [1.0 - quad.orthant_block(prob.t(j), st["sizes"], st["rho_in"], st["rho_out"]) for j in idx]
-    assert_band(out["p"], exact, 10_000_000, idx)
+    report("c5 FP32 vs block quadrature (64 designs x 1e7 draws)", **assert_band(out["p"], exact, 10_000_000, idx))
     sub = prob.subset(idx)
     out64 = run(ctx, sub, seed=0, fp64=True)
-    assert_band(out64["p"], exact, 10_000_000, list(range(len(idx))))
+    report("c5 FP64 path vs block quadrature (64 designs x 1e7 draws)",
+           **assert_band(out64["p"], exact, 10_000_000, list(range(len(idx)))))
     # same stream: the FP32 and FP64 paths agree up to the ambiguous draws of the first 2e5
     short = prob.subset(idx[:8])
     short.n_draws = np.full(8, 200_000, np.uint64)
     o32 = run(ctx, short, seed=0)
     o64 = run(ctx, short, seed=0, fp64=True)
     ora = oracle_same_stream(short, 0, range(8))
-    assert_discordance(o32["hits"], ora, list(range(8)))
-    assert_discordance(o64["hits"], oracle_same_stream(short, 0, range(8), eps=EPS64), list(range(8)))
+    report("c5 FP32 same stream (8 designs x 2e5 draws)", **assert_discordance(o32["hits"], ora, list(range(8))))
+    report("c5 FP64 same stream (8 designs x 2e5 draws, eps 1e-9)",
+           **assert_discordance(o64["hits"], oracle_same_stream(short, 0, range(8), eps=EPS64), list(range(8))))
 
 
 def test_c3_persistent_vs_per_design(ctx):
@@ -114,7 +116,7 @@ def test_c3_persistent_vs_per_design(ctx):
         single = run(ctx, prob.subset([j]), seed=0)
         assert int(single["hits"][0]) == int(batched["hits"][j])
     ora = oracle_same_stream(prob, 0, idx[:12])
-    assert_discordance(batched["hits"], ora, idx[:12])
+    report("c3 same stream (12 designs, full draw counts)", **assert_discordance(batched["hits"], ora, idx[:12]))
 
 
 def test_paper_optimal_designs_on_gpu(ctx):
@@ -124,6 +126,6 @@ def test_paper_optimal_designs_on_gpu(ctx):
     prob = workloads.paper_optima(n_draws=10_000_000)
     out = run(ctx, prob, seed=0)
     exact = [1.0 - quad.orthant_dense(prob.t(j), prob.sigmas[j]) for j in range(3)]
-    assert_band(out["p"], exact, 10_000_000, [0, 1, 2])
+    report("paper optima vs quadrature (3 designs x 1e7 draws)", **assert_band(out["p"], exact, 10_000_000, [0, 1, 2]))
     assert abs(out["p"][0] - 0.6847) <= 5e-3
     assert abs(out["p"][2] - 0.977) <= 1e-3
