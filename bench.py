@@ -134,8 +134,11 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ CPU oracle
-def cpu_oracle_rate(prob, seconds, h=0.01, seed=0):
-    """Time the FP64 oracle (as it stands) on a sample of the workload's designs."""
+def cpu_oracle_rate(prob, seconds, h=0.01, seed=0, gpu_hits=None):
+    """Time the FP64 oracle (as it stands) on a sample of the workload's designs.
+    With gpu_hits (the GPU step's hit counts at the same seed), also report
+    the GPU's error against the oracle on those designs: same counters, so
+    the counts differ only by draws whose FP32 and FP64 indicators disagree."""
     from oracle import mc as omc
     rng = np.random.default_rng(123)
     idx = rng.choice(prob.n_design, 64, replace=False)
@@ -151,11 +154,21 @@ def cpu_oracle_rate(prob, seconds, h=0.01, seed=0):
     designs = [{"Sigma": prob.sigmas[prob.design_scen[j]], "t": prob.t(j), "key": int(prob.keys[j]),
                 "n_draws": n} for j in idx]
     t0 = time.perf_counter()
-    omc.mc_batch(designs, seed, h=h, grad=True)
+    ora = omc.mc_batch(designs, seed, h=h, grad=True)
     dt = time.perf_counter() - t0
-    return {"value": n_des * n / dt, "unit": UNIT, "cores": omc.num_threads(), "kind": "oracle",
-            "sample": "%d random designs of the d=3 grid x %d draws each (their full draw count), "
-                      "FP64 estimator with adjoint sums, %.1f s" % (n_des, n, dt)}
+    rec = {"value": n_des * n / dt, "unit": UNIT, "cores": omc.num_threads(), "kind": "oracle",
+           "sample": "%d random designs of the d=3 grid x %d draws each (their full draw count), "
+                     "FP64 estimator with adjoint sums, %.1f s" % (n_des, n, dt)}
+    if gpu_hits is not None:
+        g = np.asarray(gpu_hits, dtype=np.int64)[idx]
+        o = np.asarray(ora["hits"], dtype=np.int64)
+        diff = np.abs(g - o)
+        p = o / float(n)
+        se = np.sqrt(np.maximum(p * (1.0 - p), 1e-300) / n)
+        rec["gpu_vs_oracle"] = {"designs": int(n_des), "seed": seed, "designs_differing": int(np.count_nonzero(diff)),
+                                "max_abs_hit_diff": int(diff.max()), "total_abs_hit_diff": int(diff.sum()),
+                                "max_abs_p_diff_over_se": float(np.max(diff / float(n) / se))}
+    return rec
 
 
 # ------------------------------------------------------------ reference
@@ -367,7 +380,10 @@ def run_ours(args, rank, world):
     if not args.no_extras:
         extras = run_extras(pkg, ctx, prob)
 
-    cpu = cpu_oracle_rate(prob, args.cpu_seconds)
+    out0, _ = step(0)                       # the first timed step's seed, for the oracle comparison
+    hits0 = out0["hits"].cpu().numpy()
+    ctx.sync_status()
+    cpu = cpu_oracle_rate(prob, args.cpu_seconds, gpu_hits=hits0)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

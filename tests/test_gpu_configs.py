@@ -129,3 +129,41 @@ def test_paper_optimal_designs_on_gpu(ctx):
     report("paper optima vs quadrature (3 designs x 1e7 draws)", **assert_band(out["p"], exact, 10_000_000, [0, 1, 2]))
     assert abs(out["p"][0] - 0.6847) <= 5e-3
     assert abs(out["p"][2] - 0.977) <= 1e-3
+
+
+def test_smoothing_full_size_sample(ctx):
+    """The smoothing throughput case (4096 grids of 256 x 256 FP64 values,
+    bandwidth 3, local quadratic): three whole grids against the oracle, and
+    on every grid the argmax properties that hold at any size (the reported
+    index is the lowest row-major index of the largest smoothed value, the
+    reported value is that output; the same for the raw values)."""
+    import torch
+
+    import paper_2005_10494_gb300 as pkg
+    from oracle import smooth
+    S, G = 4096, 256
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    v = torch.rand(S * G * G, dtype=torch.float64, device="cuda", generator=gen)
+    r = pkg.mc_smooth_argmax(ctx, v, S, G, G, bandwidth=3.0, degree=2, raw=True)
+    ctx.sync_status()
+    sm = r["smoothed"].view(S, G * G)
+    idx = r["argmax_idx"].to(torch.int64)
+    vals = v.view(S, G * G)
+    top = sm.max(dim=1).values
+    first = (sm == top[:, None]).to(torch.int8).argmax(dim=1)
+    assert torch.equal(idx, first)
+    assert torch.equal(r["argmax_val"], top)
+    rtop = vals.max(dim=1).values
+    rfirst = (vals == rtop[:, None]).to(torch.int8).argmax(dim=1)
+    assert torch.equal(r["raw_idx"].to(torch.int64), rfirst)
+    assert torch.equal(r["raw_val"], rtop)
+    worst = 0.0
+    for s in (0, 2047, S - 1):
+        ref = smooth.smooth_grid(vals[s].cpu().numpy().reshape(G, G), 3.0, 2)
+        got = sm[s].cpu().numpy().reshape(G, G)
+        err = float(np.max(np.abs(got - ref)))
+        worst = max(worst, err)
+        assert err <= 2e-6
+        assert ref.ravel()[int(idx[s])] >= ref.max() - 4e-6
+    report("smoothing 4096 x 256 x 256 (3 whole grids vs the oracle, argmax properties on all)",
+           designs=3 * G * G, max_abs_err=worst)
