@@ -65,6 +65,71 @@ def fp32_flops_per_draw(d, grad):
     return f
 
 
+# Operations per draw-evaluation by instruction class (one design, one draw,
+# FP32 path), counted from the estimator as the sampling kernel writes it:
+#   Philox4x32-10 per call (4 normals): 19 wide multiplies (round 1's key
+#     product is a per-tile constant), 19 xors and 1 counter add (ALU);
+#   Box-Muller per pair: 2 word-to-float shift-adds and a compare-select
+#     (ALU, 4), 6 FP32 (u0, 2v, log scale, angle, two products), and one
+#     each of lg2, sqrt, sin and cos;
+#   y = L z: d(d+1)/2 FP32; above d = 6, L comes from shared memory:
+#     sum_i ceil((i+1)/4) 16-byte loads per group of G draws (G = 1, 2 or 4
+#     draws whose normals fill whole Philox calls; the draws of a group
+#     share the loads) and t stays in registers;
+#   indicator: d compares and one count add (ALU).
+#   Adjoint per coordinate: 7 FP32 (sums A and B; sigmoid argument, 1 + e,
+#     running product, 1 - keep, sum G), ex2, rcp and, above d = 6, one
+#     shared load (the scaled threshold); one select per draw (ALU).
+# An ncu capture of the executed instructions per pipe agrees with these
+# counts within 10 % at d = 3, 10 and 20.
+def class_counts(d, grad):
+    calls, pairs = d / 4.0, d / 2.0
+    c = {"mul_wide": 19 * calls, "alu": 20 * calls + 4 * pairs + d + 1,
+         "ffma": 6 * pairs + d * (d + 1) / 2.0, "lg2": pairs, "sqrt": pairs, "sin": pairs, "cos": pairs,
+         "ex2": 0.0, "rcp": 0.0, "lds128": 0.0}
+    if d > 6:
+        group = 1 if d % 4 == 0 else (2 if d % 2 == 0 else 4)
+        c["lds128"] = sum((i + 4) // 4 for i in range(d)) / float(group)
+    if grad:
+        c["ffma"] += 7 * d
+        c["ex2"] += d
+        c["rcp"] += d
+        c["alu"] += 1
+        if d > 6:
+            c["lds128"] += d
+    return c
+
+
+MUFU = ("lg2", "sqrt", "sin", "cos", "ex2", "rcp")
+
+
+def pipe_bound(rates, d, grad, sm_count, mhz=SM_MAX_MHZ):
+    """The min-over-pipes bound on draw-evaluations per second: SM clocks per
+    draw on each pipe = the draw's operations of that pipe's classes / the
+    measured operations per SM clock (mcd_pipe_rate); the busiest pipe binds.
+    "fma_pipes" assumes wide multiplies occupy the heavy half of the FMA pipe
+    and FP32 work spreads over both halves; "issue" is one warp instruction
+    per clock per scheduler (128 operations per SM clock)."""
+    n = class_counts(d, grad)
+    half = rates["ffma"] / 2.0
+    # wide multiplies: the faster of the bare multiply-add and the multiplies
+    # inside Philox rounds as the kernels run them
+    r_mul = max(rates["mul_wide"], rates.get("philox", 0.0))
+    clk = {
+        "int_multiply": n["mul_wide"] / r_mul,
+        "alu": n["alu"] / rates["lop3"],
+        "fp32": n["ffma"] / rates["ffma"],
+        "fma_pipes": (n["mul_wide"] * half / r_mul + n["ffma"]) / rates["ffma"],
+        "mufu": sum(n[k] / rates[k] for k in MUFU),
+        "lsu": n["lds128"] / rates["lds128"],
+        "issue": sum(n.values()) / LANES,
+    }
+    binding = max(clk, key=clk.get)
+    bound = sm_count * mhz * 1e6 / clk[binding]
+    return {"sm_clk_per_draw": clk, "binding": binding, "bound_draw_evals_per_s": bound,
+            "ops_per_draw": n}
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -376,9 +441,15 @@ def run_ours(args, rank, world):
         e2e_times.append(time.perf_counter() - t0)
     e2e_value = world * draws * args.steps / sum(e2e_times)
 
+    # instruction-class rates of this GPU (own microbenchmarks), for the
+    # min-over-pipes bound
+    rates = pkg.pipe_rates(ctx, iters=4096, stream=stream)
+    pb = pipe_bound(rates, 3, True, sm_count)
+    achieved_draws = draws / (kernel_ms / 1e3)
+
     extras = {}
     if not args.no_extras:
-        extras = run_extras(pkg, ctx, prob)
+        extras = run_extras(pkg, ctx, prob, rates, sm_count)
 
     out0, _ = step(0)                       # the first timed step's seed, for the oracle comparison
     hits0 = out0["hits"].cpu().numpy()
@@ -400,6 +471,13 @@ def run_ours(args, rank, world):
                      "kernel": "sample_kernel<3,3,grad,float>", "kernel_ms": kernel_ms,
                      "ops_per_draw": ops, "peak_basis": "%d SMs x 128 lanes x %.0f MHz (max SM clock), "
                      "one 32-bit op per lane per clock" % (sm_count, SM_MAX_MHZ)},
+        "pipe_bound": {"kernel": "sample_kernel<3,3,grad,float>", "achieved": achieved_draws,
+                       "bound": pb["bound_draw_evals_per_s"], "unit": UNIT,
+                       "frac": achieved_draws / pb["bound_draw_evals_per_s"], "binding": pb["binding"],
+                       "sm_clk_per_draw": pb["sm_clk_per_draw"], "ops_per_draw": pb["ops_per_draw"],
+                       "rates_ops_per_sm_clk": rates,
+                       "basis": "draw-evaluations per second if the busiest pipe ran at the rate the "
+                                "microbenchmarks measured, at %.0f MHz" % SM_MAX_MHZ},
         "fp32_pipe": {"achieved_tflops": fp32 / 1e12, "peak_tflops": fp32_peak / 1e12, "frac": fp32 / fp32_peak,
                       "flops_per_draw": fp32_flops_per_draw(3, True)},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -625,25 +703,32 @@ def paper_optimisation(pkg, ctx):
                                                        "171 of them per condition"}}
 
 
-def run_extras(pkg, ctx, c2):
+def dim_line(rf, rg, d, rates, sm_count):
+    bf, bg = pipe_bound(rates, d, False, sm_count), pipe_bound(rates, d, True, sm_count)
+    return {"fwd": rf, "adj": rg, "adjoint_overhead": rf / rg,
+            "fwd_op_frac": rf * ops_per_draw(d, False) / (sm_count * LANES * SM_MAX_MHZ * 1e6),
+            "fwd_pipe_bound": {"binding": bf["binding"], "bound": bf["bound_draw_evals_per_s"],
+                               "frac": rf / bf["bound_draw_evals_per_s"]},
+            "adj_pipe_bound": {"binding": bg["binding"], "bound": bg["bound_draw_evals_per_s"],
+                               "frac": rg / bg["bound_draw_evals_per_s"]}}
+
+
+def run_extras(pkg, ctx, c2, rates, sm_count):
     import torch
 
     import workloads
     ex = {}
     r3f, _ = kernel_rate(pkg, ctx, c2, grad=False)
     r3g, _ = kernel_rate(pkg, ctx, c2, grad=True)
-    ex["d3"] = {"fwd": r3f, "adj": r3g, "adjoint_overhead": r3f / r3g,
-                "fwd_op_frac": r3f * ops_per_draw(3, False) / (152 * LANES * SM_MAX_MHZ * 1e6)}
+    ex["d3"] = dim_line(r3f, r3g, 3, rates, sm_count)
     c4 = workloads.c4()
     r10f, _ = kernel_rate(pkg, ctx, c4, grad=False, reps=1)
     r10g, _ = kernel_rate(pkg, ctx, c4, grad=True, reps=1)
-    ex["d10"] = {"fwd": r10f, "adj": r10g, "adjoint_overhead": r10f / r10g,
-                 "fwd_op_frac": r10f * ops_per_draw(10, False) / (152 * LANES * SM_MAX_MHZ * 1e6)}
+    ex["d10"] = dim_line(r10f, r10g, 10, rates, sm_count)
     c5 = workloads.c5()
     r20f, _ = kernel_rate(pkg, ctx, c5, grad=False, reps=1)
     r20g, _ = kernel_rate(pkg, ctx, c5, grad=True, reps=1)
-    ex["d20"] = {"fwd": r20f, "adj": r20g, "adjoint_overhead": r20f / r20g,
-                 "fwd_op_frac": r20f * ops_per_draw(20, False) / (152 * LANES * SM_MAX_MHZ * 1e6)}
+    ex["d20"] = dim_line(r20f, r20g, 20, rates, sm_count)
     # batched uneven dimensions: one persistent launch vs one launch per design
     ex["c3"] = c3_batched_vs_per_design(pkg, ctx)
     # d=10 gradient search (120 adjoint launches of 1e7 draws)

@@ -312,6 +312,38 @@ mcd_status mcd_debug_normals(mcd_ctx* ctx, uint64_t seed, uint64_t key, uint64_t
                              uint64_t count, float* z32, double* z64, uint32_t* words,
                              mcd_stream stream);
 
+/* ---- measurement --------------------------------------------------------- */
+
+/* Instruction classes of the sampling kernels, for mcd_pipe_rate. */
+#define MCD_PIPE_MUL_WIDE  0   /* mad.wide.u32: 32x32->64 multiply-add (Philox)    */
+#define MCD_PIPE_MAD_LO    1   /* mad.lo.u32: 32-bit integer multiply-add          */
+#define MCD_PIPE_LOP3      2   /* lop3.b32: three-input logic (Philox xors)        */
+#define MCD_PIPE_FFMA      3   /* fma.rn.f32 (L z, Box-Muller, adjoint sums)       */
+#define MCD_PIPE_LG2       4   /* lg2.approx.ftz.f32 (Box-Muller radius)           */
+#define MCD_PIPE_SQRT      5   /* sqrt.approx.ftz.f32 (Box-Muller radius)          */
+#define MCD_PIPE_SIN       6   /* sin.approx.ftz.f32 (Box-Muller angle)            */
+#define MCD_PIPE_COS       7   /* cos.approx.ftz.f32 (Box-Muller angle)            */
+#define MCD_PIPE_EX2       8   /* ex2.approx.ftz.f32 (sigmoid of the adjoint)      */
+#define MCD_PIPE_RCP       9   /* rcp.approx.ftz.f32 (sigmoid of the adjoint)      */
+#define MCD_PIPE_MIXED    10   /* half fma.rn.f32, half lop3.b32 (co-issue)        */
+#define MCD_PIPE_LDS128   11   /* ld.shared.v4 at a warp-uniform address (L, d > 6) */
+#define MCD_PIPE_PHILOX   12   /* Philox rounds 2..10 as sampled, per wide multiply */
+#define MCD_PIPE_COUNT    13
+
+/* Throughput of one instruction class on this device, in operations per SM
+ * clock: the median over SMs of a microbenchmark in which every thread runs
+ * eight dependency chains of that instruction, 8 blocks of 256 threads per
+ * SM, timed with the SM's cycle counter.  With the per-draw operation counts
+ * of the estimator (Sec. 2.2) this bounds draw-evaluations per clock per SM
+ * from above.
+ *   op: MCD_PIPE_*;  iters: chain steps per thread, 1 <= iters <= 2^20 (each
+ *     thread issues 8 * iters instructions of the class, 36 * iters wide
+ *     multiplies for MCD_PIPE_PHILOX);
+ *   rate (HOST [1]): operations per SM clock.
+ * Allocates and frees its own device buffers on the stream and synchronises
+ * it.  MCD_EINVAL for an unknown op or iters out of range. */
+mcd_status mcd_pipe_rate(mcd_ctx* ctx, int32_t op, int32_t iters, double* rate, mcd_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

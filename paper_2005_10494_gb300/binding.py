@@ -18,6 +18,8 @@ MCD_OK, MCD_EINVAL, MCD_ENOTSPD, MCD_ECUDA, MCD_ENOMEM, MCD_EUNSUPPORTED, MCD_EN
 MCD_ANY_EXCEEDS, MCD_ALL_BELOW = 0, 1
 MCD_PLAN_GRAD, MCD_PLAN_AUTOTUNE, MCD_PLAN_GRAPH, MCD_PLAN_FP64, MCD_PLAN_TIMING, MCD_PLAN_SHARED = 1, 2, 4, 8, 16, 32
 MCD_SHARED_MIN = 32
+# instruction classes of mcd_pipe_rate, in MCD_PIPE_* order
+PIPE_CLASSES = ("mul_wide", "mad_lo", "lop3", "ffma", "lg2", "sqrt", "sin", "cos", "ex2", "rcp", "mixed", "lds128", "philox")
 MCD_MAX_D = 20
 
 _c_i32p = ctypes.POINTER(ctypes.c_int32)
@@ -73,6 +75,7 @@ def load(path=LIB_PATH):
         "mc_tps_gcv": (i32, [vp, i32, i32, vp, vp, i32, ctypes.POINTER(f64), vp, vp]),
         "mcd_debug_normals": (i32, [vp, u64, u64, u64, u64, vp, vp, vp, vp]),
         "mc_design_eval_noalloc": (i32, [ctypes.c_int, ctypes.POINTER(CProblem), u64, vp, vp, vp, vp]),
+        "mcd_pipe_rate": (i32, [vp, i32, i32, ctypes.POINTER(f64), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -389,3 +392,14 @@ def debug_normals(ctx, seed, key, m_begin, count, stream=None):
     ctx.check(ctx.lib.mcd_debug_normals(ctx.handle, seed, key, m_begin, count, _ptr(z32), _ptr(z64),
                                         _ptr(words), _stream(stream)))
     return z32[:count], z64[:count], words[:4 * ncalls]
+
+
+def pipe_rates(ctx, iters=4096, classes=PIPE_CLASSES, stream=None):
+    """Operations per SM clock of each instruction class (mcd_pipe_rate)."""
+    out = {}
+    for name in classes:
+        r = ctypes.c_double(0.0)
+        ctx.check(ctx.lib.mcd_pipe_rate(ctx.handle, PIPE_CLASSES.index(name), int(iters), ctypes.byref(r),
+                                        _stream(stream)))
+        out[name] = r.value
+    return out

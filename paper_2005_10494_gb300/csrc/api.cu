@@ -17,6 +17,7 @@
 #include "fwer.cuh"
 #include "tps.cuh"
 #include "mcd_internal.cuh"
+#include "pipes.cuh"
 
 using namespace mcd;
 
@@ -1145,6 +1146,55 @@ mcd_status mcd_debug_normals(mcd_ctx* ctx, uint64_t seed, uint64_t key, uint64_t
     MCD_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
     MCD_CUDA(launch_debug_normals(seed, key, m_begin, count, z32, z64, words, reinterpret_cast<cudaStream_t>(stream)),
              "debug launch");
+    return MCD_OK;
+}
+
+mcd_status mcd_pipe_rate(mcd_ctx* ctx, int32_t op, int32_t iters, double* rate, mcd_stream stream) {
+    if (!ctx) return MCD_EINVAL;
+    if (!rate || op < 0 || op >= MCD_PIPE_COUNT || iters < 1 || iters > (1 << 20))
+        return fail(ctx, MCD_EINVAL, "pipe rate: unknown op, iters outside [1, 2^20] or NULL rate");
+    NvtxRange nv("mcd_pipe_rate");
+    MCD_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int blocks = ctx->sm_count * kPipeBlocksPerSM;
+    // t0 | t1 (i64 per block) | smid (i32 per block, padded) | sink (u32 per thread)
+    const size_t off_smid = 16 * static_cast<size_t>(blocks);
+    const size_t off_sink = off_smid + ((4 * static_cast<size_t>(blocks) + 15) / 16) * 16;
+    const size_t bytes = off_sink + 4 * static_cast<size_t>(blocks) * kPipeThreads;
+    char* ws = nullptr;
+    MCD_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&ws), bytes, s), "pipe workspace");
+    long long* t0 = reinterpret_cast<long long*>(ws);
+    long long* t1 = t0 + blocks;
+    int* smid = reinterpret_cast<int*>(ws + off_smid);
+    uint32_t* sink = reinterpret_cast<uint32_t*>(ws + off_sink);
+    std::vector<long long> h0(blocks), h1(blocks);
+    std::vector<int> hs(blocks);
+    // a short warm-up launch, then the timed one
+    cudaError_t e = launch_pipe(op, std::min(iters, 64), blocks, kPhiloxM0, 0.5f, sink, t0, t1, smid, s);
+    if (e == cudaSuccess) e = launch_pipe(op, iters, blocks, kPhiloxM0, 0.5f, sink, t0, t1, smid, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h0.data(), t0, 8 * static_cast<size_t>(blocks), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h1.data(), t1, 8 * static_cast<size_t>(blocks), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), smid, 4 * static_cast<size_t>(blocks), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(ws, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "pipe microbenchmark");
+    // per SM: first start, last end, blocks
+    std::vector<long long> lo(ctx->sm_count, 0), hi(ctx->sm_count, 0);
+    std::vector<int> nb(ctx->sm_count, 0);
+    for (int b = 0; b < blocks; ++b) {
+        const int m = hs[b];
+        if (m < 0 || m >= ctx->sm_count) continue;
+        if (nb[m] == 0 || h0[b] < lo[m]) lo[m] = h0[b];
+        if (nb[m] == 0 || h1[b] > hi[m]) hi[m] = h1[b];
+        ++nb[m];
+    }
+    std::vector<double> r;
+    const double ops_per_block = static_cast<double>(kPipeThreads) * pipe_ops_per_step(op) * iters;
+    for (int m = 0; m < ctx->sm_count; ++m)
+        if (nb[m] > 0 && hi[m] > lo[m]) r.push_back(ops_per_block * nb[m] / static_cast<double>(hi[m] - lo[m]));
+    if (r.empty()) return fail(ctx, MCD_ECUDA, "pipe microbenchmark: no SM reported a positive cycle count");
+    std::sort(r.begin(), r.end());
+    *rate = (r.size() % 2) ? r[r.size() / 2] : 0.5 * (r[r.size() / 2 - 1] + r[r.size() / 2]);
     return MCD_OK;
 }
 

@@ -78,14 +78,35 @@ __device__ __forceinline__ double fmadd(double a, double b, double c) { return _
 // Shared-memory vector loads that the compiler may not hoist out of the draw
 // loop (volatile), so large factors are streamed from shared memory instead
 // of being pinned in registers.
+template <bool VOL>
 __device__ __forceinline__ void lds_vec(const float* p, float* v) {
     const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(p));
-    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "r"(a));
+    if constexpr (VOL)
+        asm volatile("ld.volatile.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "r"(a));
+    else
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "r"(a));
 }
+template <bool VOL>
 __device__ __forceinline__ void lds_vec(const double* p, double* v) {
     const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(p));
-    asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v[0]), "=d"(v[1]) : "r"(a));
+    if constexpr (VOL)
+        asm volatile("ld.volatile.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v[0]), "=d"(v[1]) : "r"(a));
+    else
+        asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v[0]), "=d"(v[1]) : "r"(a));
+}
+__device__ __forceinline__ float lds_one(const float* p) {
+    const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(p));
+    float v;
+    asm volatile("ld.volatile.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ double lds_one(const double* p) {
+    const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(p));
+    double v;
+    asm volatile("ld.volatile.shared.f64 %0, [%1];" : "=d"(v) : "r"(a));
+    return v;
 }
 
 // sigma((t - y)/h) = 1 / (1 + exp((y - t)/h)).
@@ -95,6 +116,19 @@ __device__ __forceinline__ float smooth_keep(float y, float t, float tsc, float 
 }
 static __device__ __noinline__ double smooth_keep(double y, double t, float, float, double hinv) {
     return 1.0 / (1.0 + exp((y - t) * hinv));
+}
+
+// Above d = 6 the factor is read from shared memory for every draw.  Plain
+// ld.shared lets the compiler share a load between the draws of a group and
+// keep thresholds in registers; ld.volatile.shared makes every draw load
+// again but frees those registers.  In the FP32 adjoint kernels the second
+// form avoids register spills, and it measured faster on GB300 (64 designs
+// x 2e6 draws, AR(1) factor) at d = 8..12 and 15..19 by 4-42 %; at d = 7,
+// 13, 14 and 20, and in every forward kernel, the plain form is as fast or
+// faster.
+template <int D, bool GRAD, typename R>
+__host__ __device__ constexpr bool volatile_loads() {
+    return GRAD && sizeof(R) == 4 && ((D >= 8 && D <= 12) || (D >= 15 && D <= 19));
 }
 
 // Factor, thresholds and bandwidth of the current tile, as one draw sees them.
@@ -112,7 +146,7 @@ struct TileView {
 };
 
 // y_i = sum_{j <= i} L_ij z_j for row i.
-template <int D, int I, typename R>
+template <int D, int I, bool VOL, typename R>
 __device__ __forceinline__ R row_dot(const TileView<D, R>& v, const R* z) {
     constexpr int V = LPad<R>::V;
     constexpr int off = LPad<R>::rowoff(I);
@@ -123,13 +157,13 @@ __device__ __forceinline__ R row_dot(const TileView<D, R>& v, const R* z) {
         for (int j = 1; j <= I; ++j) s = fmadd(v.L[off + j], z[j], s);
     } else {
         R l[V];
-        lds_vec(v.sL + off, l);
+        lds_vec<VOL>(v.sL + off, l);
         s = l[0] * z[0];
 #pragma unroll
         for (int j = 1; j < V && j <= I; ++j) s = fmadd(l[j], z[j], s);
 #pragma unroll
         for (int c = 1; c * V <= I; ++c) {
-            lds_vec(v.sL + off + c * V, l);
+            lds_vec<VOL>(v.sL + off + c * V, l);
 #pragma unroll
             for (int q = 0; q < V && c * V + q <= I; ++q) s = fmadd(l[q], z[c * V + q], s);
         }
@@ -142,12 +176,16 @@ struct Rows {
     // Walk rows I..D-1: hit test, and the smoothed-indicator factors.
     __device__ __forceinline__ static void run(const TileView<D, R>& v, const R* z, bool& hit,
                                                R* keep, R& prod) {
-        const R y = row_dot<D, I, R>(v, z);
+        constexpr bool VOL = volatile_loads<D, GRAD, R>();
+        const R y = row_dot<D, I, VOL, R>(v, z);
         R t;
         float tsc = 0.0f;
         if constexpr (TileView<D, R>::kReg) {
             t = v.t[I];
             if constexpr (GRAD) tsc = v.tsc[I];
+        } else if constexpr (VOL) {
+            t = lds_one(v.st + I);
+            tsc = lds_one(v.stsc + I);
         } else {
             t = v.st[I];
             if constexpr (GRAD) tsc = v.stsc[I];

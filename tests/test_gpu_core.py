@@ -381,3 +381,25 @@ def test_smoothing_of_an_unaligned_input(ctx):
         np.testing.assert_array_equal(r1[k].cpu().numpy(), r2[k].cpu().numpy())
     sm_ref = smooth.smooth_argmax(vals, g1, g2, 3.0, 2)[0]
     np.testing.assert_allclose(r1["smoothed"].cpu().numpy().reshape(S, g1, g2), sm_ref, rtol=0, atol=2e-6)
+
+
+# ------------------------------------------------------------ pipe rates
+def test_pipe_rates_are_plausible(ctx):
+    """Instruction-class rates (ops per SM clock) lie within what one SM can
+    issue: four schedulers x 32 lanes, and no class reads zero."""
+    import paper_2005_10494_gb300 as pkg
+    from paper_2005_10494_gb300.binding import MCD_EINVAL, PIPE_CLASSES
+    rates = pkg.pipe_rates(ctx, iters=1024)
+    assert set(rates) == set(PIPE_CLASSES)
+    for name, r in rates.items():
+        assert 1.0 <= r <= 128.0 * 1.02, (name, r, rates)
+    # FP32 FMA runs on both halves of the FMA pipe; a mix of FMA and logic
+    # instructions issues at least as fast as either alone.
+    assert rates["ffma"] >= 60.0
+    assert rates["mixed"] >= 0.95 * min(rates["ffma"], rates["lop3"])
+    again = pkg.pipe_rates(ctx, iters=4096, classes=("ffma", "lg2"))
+    for name in again:
+        assert again[name] == pytest.approx(rates[name], rel=0.1)
+    with pytest.raises(pkg.MCDError) as e:
+        pkg.pipe_rates(ctx, iters=0, classes=("ffma",))
+    assert e.value.code == MCD_EINVAL
