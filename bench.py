@@ -79,7 +79,9 @@ def fp32_flops_per_draw(d, grad):
 #   indicator: d compares and one count add (ALU).
 #   Adjoint per coordinate: 7 FP32 (sums A and B; sigmoid argument, 1 + e,
 #     running product, 1 - keep, sum G), ex2, rcp and, above d = 6, one
-#     shared load (the scaled threshold); one select per draw (ALU).
+#     shared load (the scaled threshold); one select per draw (ALU).  At the
+#     dimensions where the adjoint reloads with volatile loads, every draw
+#     loads all chunks of L and both thresholds.
 # An ncu capture of the executed instructions per pipe agrees with these
 # counts within 10 % at d = 3, 10 and 20.
 def class_counts(d, grad):
@@ -87,8 +89,11 @@ def class_counts(d, grad):
     c = {"mul_wide": 19 * calls, "alu": 20 * calls + 4 * pairs + d + 1,
          "ffma": 6 * pairs + d * (d + 1) / 2.0, "lg2": pairs, "sqrt": pairs, "sin": pairs, "cos": pairs,
          "ex2": 0.0, "rcp": 0.0, "lds128": 0.0}
+    # adjoint kernels that reload the factor (and both thresholds) for
+    # every draw: the dimensions of volatile_loads() in sample.cuh
+    reload = grad and (8 <= d <= 12 or 15 <= d <= 19)
     if d > 6:
-        group = 1 if d % 4 == 0 else (2 if d % 2 == 0 else 4)
+        group = 1 if (d % 4 == 0 or reload) else (2 if d % 2 == 0 else 4)
         c["lds128"] = sum((i + 4) // 4 for i in range(d)) / float(group)
     if grad:
         c["ffma"] += 7 * d
@@ -96,7 +101,7 @@ def class_counts(d, grad):
         c["rcp"] += d
         c["alu"] += 1
         if d > 6:
-            c["lds128"] += d
+            c["lds128"] += 2 * d if reload else d
     return c
 
 
