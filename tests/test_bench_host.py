@@ -1,0 +1,92 @@
+"""Host logic of bench.py on CPU: the per-draw operation counts and the
+min-over-pipes bound, the traffic record and the clock summary."""
+import hashlib
+
+import pytest
+
+import bench
+
+
+def test_class_counts_d3():
+    f = bench.class_counts(3, False)
+    # Philox: 3/4 call per draw, 19 wide multiplies and 20 ALU ops per call;
+    # Box-Muller: 3/2 pairs, 4 ALU + 6 FP32 + 4 MUFU each; L z: 6 FP32;
+    # indicator: 3 compares + 1 count add
+    assert f["mul_wide"] == pytest.approx(14.25)
+    assert f["alu"] == pytest.approx(15 + 6 + 4)
+    assert f["ffma"] == pytest.approx(9 + 6)
+    for k in ("lg2", "sqrt", "sin", "cos"):
+        assert f[k] == pytest.approx(1.5)
+    assert f["ex2"] == f["rcp"] == f["lds128"] == 0
+    g = bench.class_counts(3, True)
+    assert g["ffma"] == pytest.approx(15 + 21)
+    assert g["ex2"] == g["rcp"] == 3
+    assert g["alu"] == pytest.approx(26)
+    assert sum(g.values()) == pytest.approx(88.25)
+
+
+@pytest.mark.parametrize("d,grad,lds", [
+    (10, False, 18 / 2),        # factor chunks shared by the 2 draws of a group
+    (10, True, 18 + 2 * 10),    # volatile reloads: every chunk and both thresholds
+    (13, True, 28 / 4 + 13),    # plain loads, groups of 4 draws, scaled thresholds
+    (20, False, 60),
+    (20, True, 60 + 20),
+    (6, True, 0),               # factor in registers
+])
+def test_class_counts_shared_loads(d, grad, lds):
+    assert bench.class_counts(d, grad)["lds128"] == pytest.approx(lds)
+
+
+def test_pipe_bound_picks_the_busiest_pipe():
+    rates = {"mul_wide": 25.0, "philox": 30.0, "mad_lo": 64.0, "lop3": 64.0, "ffma": 128.0,
+             "lg2": 16.0, "sqrt": 16.0, "sin": 16.0, "cos": 16.0, "ex2": 32.0, "rcp": 16.0,
+             "mixed": 124.0, "lds128": 16.0}
+    b = bench.pipe_bound(rates, 3, True, 152, mhz=2000.0)
+    n = bench.class_counts(3, True)
+    issue = sum(n.values()) / 128.0
+    mufu = sum(n[k] / rates[k] for k in bench.MUFU)
+    assert b["sm_clk_per_draw"]["issue"] == pytest.approx(issue)
+    assert b["sm_clk_per_draw"]["mufu"] == pytest.approx(mufu)
+    # the wide multiplies take the faster of the two measured rates
+    assert b["sm_clk_per_draw"]["int_multiply"] == pytest.approx(n["mul_wide"] / 30.0)
+    assert b["binding"] == "issue"
+    assert b["bound_draw_evals_per_s"] == pytest.approx(152 * 2000e6 / issue)
+    slow = dict(rates, sin=2.0)
+    b2 = bench.pipe_bound(slow, 3, True, 152, mhz=2000.0)
+    assert b2["binding"] == "mufu"
+    assert b2["bound_draw_evals_per_s"] < b["bound_draw_evals_per_s"]
+
+
+def test_traffic_record_scales_per_tile_and_checks_the_sources(tmp_path, monkeypatch):
+    h = hashlib.sha256()
+    for p in bench.KERNEL_SOURCES:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    rec = tmp_path / "traffic.txt"
+    rec.write_text("# comment: with a colon\nsrc_sha256: %s\ndram_bytes_read_small: 1500\n"
+                   "dram_bytes_write_small: 500\ntiles_small: 100\n" % h.hexdigest())
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(rec))
+    assert bench.traffic_record(1000) == pytest.approx(20000.0)
+    rec.write_text("src_sha256: %s\ndram_bytes_read_small: 1500\ndram_bytes_write_small: 500\n"
+                   "tiles_small: 100\n" % ("0" * 64))
+    assert bench.traffic_record(1000) is None
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(tmp_path / "missing.txt"))
+    assert bench.traffic_record(1000) is None
+
+
+def test_committed_traffic_record_matches_the_sources():
+    assert bench.traffic_record(1024) is not None
+
+
+def test_clock_summary():
+    lines = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "0, 2040, 2070, 1100.0, 0x4, Not Active, Not Active, Not Active, Active",
+             "0, 2070, 2070, 1000.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "garbage",
+             "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    c = bench.ClockSampler.summarise(lines)
+    assert c["sm_mhz"] == 2070.0
+    assert c["sm_max_mhz"] == 2070.0
+    assert c["reasons"] == ["sw_power_cap"]
+    assert c["samples"] == 3
+    assert bench.ClockSampler.summarise([])["sm_mhz"] is None
