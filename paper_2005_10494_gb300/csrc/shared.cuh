@@ -90,6 +90,52 @@ __device__ __forceinline__ void load_row(const float* p, float* v) {
     }
 }
 
+// Test the batch's nb draws (y, and z for the adjoint, in shared memory)
+// against this thread's first NQ designs.  y_i > t_i exactly when the FP32
+// difference t_i - y_i is negative: two unequal floats never subtract to
+// zero (gradual underflow), rounding keeps the sign, and the infinities
+// (dropped tests, draws outside the range) give +inf.  So the hit is the sign
+// bit of the or of the differences: FADDs and one or per draw instead of a
+// compare and a predicate merge per coordinate.  The draw loop is unrolled
+// (8 draws forward, 4 with the adjoint's larger bodies).
+template <int D, bool GRAD, int DPT, int NQ>
+__device__ __forceinline__ void test_draws(const float* sy, const float* sz, int nb, const float (&t)[DPT][D],
+                                           const float (&tsc)[DPT][GRAD ? D : 1], float hl2e, uint32_t (&cnt)[DPT],
+                                           float (&A)[DPT][GRAD ? D : 1], float (&G)[DPT][GRAD ? D : 1]) {
+    constexpr int DP = SharedShape<D, GRAD>::kDP;
+    constexpr int kUnroll = GRAD ? 4 : 8;
+#pragma unroll kUnroll
+    for (int dn = 0; dn < nb; ++dn) {
+        float y[DP];
+        load_row<DP>(sy + dn * DP, y);
+        float zz[GRAD ? DP : 4];
+        if constexpr (GRAD) load_row<DP>(sz + dn * DP, zz);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            uint32_t sgn = 0u;
+#pragma unroll
+            for (int i = 0; i < D; ++i) sgn |= __float_as_uint(__fsub_rn(t[q][i], y[i]));
+            const uint32_t hit = sgn >> 31;
+            cnt[q] += hit;
+            if constexpr (GRAD) {
+                const float hv = hit ? 1.0f : 0.0f;
+#pragma unroll
+                for (int i = 0; i < D; ++i) A[q][i] = fmadd(hv, zz[i], A[q][i]);
+                if (hl2e != 0.0f) {
+                    float keep[D], prod = 1.0f;
+#pragma unroll
+                    for (int i = 0; i < D; ++i) {
+                        keep[i] = smooth_keep(y[i], t[q][i], tsc[q][i], hl2e, 0.0);
+                        prod *= keep[i];
+                    }
+#pragma unroll
+                    for (int i = 0; i < D; ++i) G[q][i] = fmadd(prod, 1.0f - keep[i], G[q][i]);
+                }
+            }
+        }
+    }
+}
+
 template <int D, bool GRAD>
 __global__ void __launch_bounds__(kSharedThreads) shared_kernel(const __grid_constant__ SampleParams P,
                                                                 const SharedTile* __restrict__ tiles,
@@ -166,41 +212,14 @@ __global__ void __launch_bounds__(kSharedThreads) shared_kernel(const __grid_con
                                 gi * S::kG, ofs, gi < ngroups ? tl.n : 0u, sy, sz, bsum);
             __syncthreads();
             const int nb = static_cast<int>(min(static_cast<uint32_t>(SS::kBD), (ngroups - g0) * S::kG));
-            for (int dn = 0; dn < nb; ++dn) {
-                float y[DP];
-                load_row<DP>(sy + dn * DP, y);
-                float zz[GRAD ? DP : 4];
-                if constexpr (GRAD) load_row<DP>(sz + dn * DP, zz);
-#pragma unroll
-                for (int q = 0; q < DPT; ++q) {
-                    if (q >= nq) break;
-                    // y_i > t_i exactly when the FP32 difference t_i - y_i is
-                    // negative: two unequal floats never subtract to zero
-                    // (gradual underflow), rounding keeps the sign, and the
-                    // infinities (dropped tests, draws outside the range)
-                    // give +inf.  So the hit is the sign bit of the or of the
-                    // differences: FADDs and one or per draw instead of a
-                    // compare and a predicate merge per coordinate.
-                    uint32_t sgn = 0u;
-#pragma unroll
-                    for (int i = 0; i < D; ++i) sgn |= __float_as_uint(__fsub_rn(t[q][i], y[i]));
-                    const uint32_t hit = sgn >> 31;
-                    cnt[q] += hit;
-                    if constexpr (GRAD) {
-                        const float hv = hit ? 1.0f : 0.0f;
-#pragma unroll
-                        for (int i = 0; i < D; ++i) A[q][i] = fmadd(hv, zz[i], A[q][i]);
-                        if (hl2e != 0.0f) {
-                            float keep[D], prod = 1.0f;
-#pragma unroll
-                            for (int i = 0; i < D; ++i) {
-                                keep[i] = smooth_keep(y[i], t[q][i], tsc[q][i], hl2e, 0.0);
-                                prod *= keep[i];
-                            }
-#pragma unroll
-                            for (int i = 0; i < D; ++i) G[q][i] = fmadd(prod, 1.0f - keep[i], G[q][i]);
-                        }
-                    }
+            // nq is block-uniform: one branch per batch picks the loop for
+            // exactly nq designs per thread
+            if (nq >= DPT) test_draws<D, GRAD, DPT, DPT>(sy, sz, nb, t, tsc, hl2e, cnt, A, G);
+            else if constexpr (DPT > 1) {
+                if (nq == 1) test_draws<D, GRAD, DPT, 1>(sy, sz, nb, t, tsc, hl2e, cnt, A, G);
+                else if constexpr (DPT > 2) {
+                    if (nq == 2) test_draws<D, GRAD, DPT, 2>(sy, sz, nb, t, tsc, hl2e, cnt, A, G);
+                    else if constexpr (DPT > 3) test_draws<D, GRAD, DPT, 3>(sy, sz, nb, t, tsc, hl2e, cnt, A, G);
                 }
             }
             __syncthreads();                          // the next batch rewrites sy / sz
