@@ -661,6 +661,34 @@ def c2_shared(pkg, ctx, c2):
     return res
 
 
+def c5_fp64(pkg, ctx):
+    """C5 (d=20) on its 64-design subsample at 1e7 draws per design: the
+    all-FP64 sampling path against the FP32 path on the same streams."""
+    import workloads
+    c5 = workloads.c5()
+    sub = c5.subset(workloads.c5_subsample().tolist())
+    res, hits = {}, {}
+    for name, fp64 in (("fp32", False), ("fp64", True)):
+        dp = pkg.DeviceProblem.from_workload(sub)
+        plan = pkg.Plan(ctx, dp, fp64=fp64, timing=True)
+        best = 1e30
+        for r in range(3):
+            out = plan.eval(200)
+            ms = plan.kernel_ms()
+            if r > 0:
+                best = min(best, ms)
+        hits[name] = out["hits"].cpu().numpy().astype(np.int64)
+        res[name] = {"ms": best, "draw_evals_per_s": sub.total_draws() / (best / 1e3)}
+        plan.close()
+    ctx.sync_status()
+    diff = np.abs(hits["fp32"] - hits["fp64"])
+    res["fp64_over_fp32_time"] = res["fp64"]["ms"] / res["fp32"]["ms"]
+    res["same_stream_hits"] = {"designs": int(diff.size), "designs_differing": int(np.count_nonzero(diff)),
+                               "max_abs_diff": int(diff.max()), "total_abs_diff": int(diff.sum()),
+                               "draws_per_design": int(sub.n_draws[0])}
+    return res
+
+
 def fwer_calibration(pkg, ctx, n=10_000_000, rounds=14):
     """Eq. 2 on the device: the alpha scale of every split of the d=3 grid's
     16 scenarios x 129 allocations, 1e7 draws per evaluation, against the
@@ -740,6 +768,8 @@ def run_extras(pkg, ctx, c2, rates, sm_count):
     r20f, _ = kernel_rate(pkg, ctx, c5, grad=False, reps=1)
     r20g, _ = kernel_rate(pkg, ctx, c5, grad=True, reps=1)
     ex["d20"] = dim_line(r20f, r20g, 20, rates, sm_count)
+    # the all-FP64 sampling path (C5 subsample) against the FP32 path
+    ex["c5_fp64"] = c5_fp64(pkg, ctx)
     # batched uneven dimensions: one persistent launch vs one launch per design
     ex["c3"] = c3_batched_vs_per_design(pkg, ctx)
     # d=10 gradient search (120 adjoint launches of 1e7 draws)
