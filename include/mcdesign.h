@@ -296,7 +296,8 @@ mcd_status mc_tps_argmax(mcd_ctx* ctx, int32_t n_surf, int32_t n_pts, int32_t k,
  *     largest smoothed value, and that value;
  *   raw_idx / raw_val (DEVICE [S], may be NULL): the same for the input.
  * Needs g1, g2 >= 1 and, along each smoothed axis, at least degree + 1
- * points within every window. */
+ * points within every window.  Limits: g1 * g2 < 2^31, n_scen <= 65535 and,
+ * for 2-D grids, g1 <= 65535 * 32; beyond them MCD_EINVAL. */
 mcd_status mc_smooth_argmax(mcd_ctx* ctx, int32_t n_scen, int32_t g1, int32_t g2,
                             const double* value, double bandwidth, int32_t degree,
                             double* smoothed, int64_t* argmax_idx, double* argmax_val,

@@ -18,6 +18,7 @@
 #include "tps.cuh"
 #include "mcd_internal.cuh"
 #include "pipes.cuh"
+#include "smooth.cuh"
 
 using namespace mcd;
 
@@ -1114,6 +1115,7 @@ mcd_status mc_smooth_argmax(mcd_ctx* ctx, int32_t n_scen, int32_t g1, int32_t g2
     if (!ctx) return MCD_EINVAL;
     if (n_scen < 1 || g1 < 1 || g2 < 1) return fail(ctx, MCD_EINVAL, "n_scen, g1, g2 must be >= 1");
     if (static_cast<int64_t>(g1) * g2 >= (1ll << 31)) return fail(ctx, MCD_EINVAL, "grid too large");
+    if (const char* why = smooth_shape_error(n_scen, g1, g2)) return fail(ctx, MCD_EINVAL, why);
     if (!(bandwidth > 1.0 && bandwidth <= 4.0)) return fail(ctx, MCD_EINVAL, "bandwidth must be in (1, 4]");
     if (degree < 0 || degree > 2) return fail(ctx, MCD_EINVAL, "degree must be 0, 1 or 2");
     if (!value || !argmax_idx || !argmax_val) return fail(ctx, MCD_EINVAL, "value, argmax_idx, argmax_val must not be NULL");

@@ -16,6 +16,7 @@
 
 
 #include "mcd_internal.cuh"
+#include "smooth.cuh"
 
 namespace mcd {
 
@@ -646,6 +647,15 @@ int blocks_per_scen(int g1, int g2) {
 }
 
 }  // namespace
+
+const char* smooth_shape_error(int n_scen, int g1, int g2) {
+    // launch limits: scenarios on gridDim.z (2-D) or gridDim.y (1-D), and
+    // in 2-D the rows of blocks on gridDim.y, each at most 65535
+    if (n_scen > 65535) return "at most 65535 scenarios per call";
+    if (g1 > 1 && g2 > 1 && (g1 + kRowsPerBlock - 1) / kRowsPerBlock > 65535)
+        return "g1 too large for the 2-D stencil (at most 65535 * 32 rows)";
+    return nullptr;
+}
 
 size_t smooth_weight_count() {
     return static_cast<size_t>(kClassSlots) * kMaxTaps + kIntSlot;

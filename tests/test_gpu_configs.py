@@ -167,3 +167,70 @@ def test_smoothing_full_size_sample(ctx):
         assert ref.ravel()[int(idx[s])] >= ref.max() - 4e-6
     report("smoothing 4096 x 256 x 256 (3 whole grids vs the oracle, argmax properties on all)",
            designs=3 * G * G, max_abs_err=worst)
+
+
+def test_smoothing_size_limits(ctx):
+    """The stencil at its limits: 65535 scenarios, and one grid of
+    46340 x 46341 points (just below 2^31), checked on sampled points
+    against the oracle and by the argmax properties over every output;
+    shapes beyond the launch limits are refused on the host."""
+    import torch
+
+    import paper_2005_10494_gb300 as pkg
+    from paper_2005_10494_gb300.binding import MCD_EINVAL
+    from oracle import smooth
+    small = torch.zeros(8, dtype=torch.float64, device="cuda")
+    for S, g1, g2 in ((65536, 5, 5), (1, 65535 * 32 + 1, 2), (1, 46341, 46341)):
+        with pytest.raises(pkg.MCDError) as e:
+            pkg.mc_smooth_argmax(ctx, small, S, g1, g2, smoothed=False)
+        assert e.value.code == MCD_EINVAL
+    ctx.sync_status()
+
+    # 65535 scenarios of 5 x 5
+    S = 65535
+    gen = torch.Generator(device="cuda").manual_seed(2)
+    v = torch.rand(S * 25, dtype=torch.float64, device="cuda", generator=gen)
+    r = pkg.mc_smooth_argmax(ctx, v, S, 5, 5)
+    ctx.sync_status()
+    sm = r["smoothed"].view(S, 25)
+    top = sm.max(dim=1).values
+    assert torch.equal(r["argmax_idx"], (sm == top[:, None]).to(torch.int8).argmax(dim=1))
+    assert torch.equal(r["argmax_val"], top)
+    for s in (0, 32767, S - 1):
+        ref = smooth.smooth_grid(v[25 * s:25 * (s + 1)].cpu().numpy().reshape(5, 5), 3.0, 2)
+        np.testing.assert_allclose(sm[s].cpu().numpy().reshape(5, 5), ref, rtol=0, atol=2e-6)
+    del v, r, sm
+
+    # one grid just below 2^31 points
+    g1, g2 = 46340, 46341
+    assert g1 * g2 < 2 ** 31
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    v = torch.rand(g1 * g2, dtype=torch.float64, device="cuda", generator=gen)
+    r = pkg.mc_smooth_argmax(ctx, v, 1, g1, g2, raw=True)
+    ctx.sync_status()
+    sm = r["smoothed"]
+    top = sm.max()
+    assert int(r["argmax_idx"][0]) == int((sm == top).nonzero()[0, 0])
+    assert r["argmax_val"][0].item() == top.item()
+    rtop = v.max()
+    assert int(r["raw_idx"][0]) == int((v == rtop).nonzero()[0, 0])
+    rng = np.random.default_rng(4)
+    pts = [(0, 0), (0, g2 - 1), (g1 - 1, 0), (g1 - 1, g2 - 1), (1, 2), (g1 - 2, g2 - 3), (g1 // 2, g2 // 2),
+           (g1 - 1, g2 // 3), (g1 - 3, g2 - 1)] + [tuple(x) for x in rng.integers(0, [g1, g2], size=(24, 2))]
+    vals = v.view(g1, g2)
+    smv = sm.view(g1, g2)
+    worst = 0.0
+    for i, j in pts:
+        r0, c0 = max(0, i - 4), max(0, j - 4)
+        cut = vals[r0:min(g1, i + 5), c0:min(g2, j + 5)].cpu().numpy()
+        # a local fit sees only its window (reach 2 at bandwidth 3): the
+        # cut-out keeps 4 rows and columns around (i, j) and the grid's own
+        # edges where they are, so the oracle on it gives the same output
+        ref = smooth.smooth_grid(cut, 3.0, 2)[i - r0, j - c0]
+        err = abs(float(smv[i, j]) - ref)
+        worst = max(worst, err)
+        assert err <= 2e-6, (i, j, float(smv[i, j]), ref)
+    report("smoothing at the size limits (65535 scenarios; 46340 x 46341 grid, 33 sampled points)",
+           designs=len(pts), max_abs_err=worst)
+    del v, r, sm, vals, smv
+    torch.cuda.empty_cache()
