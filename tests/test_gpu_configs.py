@@ -6,7 +6,7 @@ import pytest
 import workloads
 from oracle import design, quad
 
-from gpu_util import EPS64, assert_band, assert_discordance, oracle_same_stream, report, run
+from gpu_util import EPS32, EPS64, assert_band, assert_discordance, oracle_same_stream, report, run
 
 pytestmark = pytest.mark.gpu
 
@@ -233,4 +233,48 @@ def test_smoothing_size_limits(ctx):
     report("smoothing at the size limits (65535 scenarios; 46340 x 46341 grid, 33 sampled points)",
            designs=len(pts), max_abs_err=worst)
     del v, r, sm, vals, smv
+    torch.cuda.empty_cache()
+
+
+def test_four_million_designs(ctx):
+    """2^22 designs of d = 3 in one plan (one tile each, ragged draw counts
+    0..700 including zeros): every count within its draws, p = hits / n,
+    66 sampled designs against the oracle on the same streams, and the
+    adjoint plan's counts equal to the forward plan's."""
+    import torch
+
+    import paper_2005_10494_gb300 as pkg
+    J, d = 1 << 22, 3
+    rng = np.random.default_rng(5)
+    n = rng.integers(0, 701, J).astype(np.uint64)
+    n[rng.choice(J, 1000, replace=False)] = 0
+    Sig = np.array([[1.0, 0.5, 0.3], [0.5, 1.0, 0.4], [0.3, 0.4, 1.0]])
+    mu = np.full((J, d), 0.3)
+    b = 1.2 + 0.6 * rng.random((J, d))
+    keys = np.arange(J, dtype=np.uint64) * 2654435761 % (1 << 40)
+    f64 = torch.float64
+    dp = pkg.DeviceProblem([d], np.zeros(J, np.int32), n, keys, torch.as_tensor(Sig.ravel(), dtype=f64).cuda(),
+                           torch.as_tensor(mu.ravel(), dtype=f64).cuda(), torch.as_tensor(b.ravel(), dtype=f64).cuda())
+    plan = pkg.Plan(ctx, dp)
+    out = plan.eval(11)
+    ctx.sync_status()
+    hits = out["hits"].cpu().numpy().astype(np.int64)
+    p = out["p"].cpu().numpy()
+    plan.close()
+    assert np.all(hits >= 0) and np.all(hits <= n.astype(np.int64))
+    assert np.all(hits[n == 0] == 0)
+    nz = n > 0
+    np.testing.assert_array_equal(p[nz], hits[nz] / n[nz].astype(np.float64))
+    idx = np.sort(rng.choice(J, 64, replace=False)).tolist() + [0, J - 1]
+    from oracle import mc
+    designs = [{"Sigma": Sig, "t": b[j] - mu[j], "key": int(keys[j]), "n_draws": int(n[j])} for j in idx]
+    ora = mc.mc_batch(designs, 11, eps=EPS32)
+    rep = assert_discordance(hits, ora, idx)
+    gplan = pkg.Plan(ctx, dp, grad=True)
+    g = gplan.grad(11, None, 0.01)
+    ctx.sync_status()
+    np.testing.assert_array_equal(g["hits"].cpu().numpy().astype(np.int64), hits)
+    gplan.close()
+    report("four million designs, ragged draw counts (66 sampled designs, same stream)", **rep)
+    del dp, out, g
     torch.cuda.empty_cache()
