@@ -23,6 +23,11 @@
  *    Pointers marked HOST are read during the call only.
  *  - Work is queued on the given stream (NULL: the legacy default stream)
  *    and the call returns without waiting for it, except where noted.
+ *  - Host threads: calls on one context may come from several threads (its
+ *    autotuning cache is locked), but the context has one error text and one
+ *    device status word, so errors of concurrent calls overwrite each other.
+ *    To keep them apart, use one context per thread; one plan must not be
+ *    launched from two threads at once.
  *  - Determinism: a hit count depends only on (seed, key, draw_begin,
  *    n_draws, d, t = b - mu); it is bit-identical across runs, plans,
  *    batchings, tile sizes and chunkings of the draw range.  Gradient sums
