@@ -428,6 +428,9 @@ mcd_status plan_build(mcd_ctx* ctx, const mcd_problem* pr, int32_t flags, int32_
         const uint32_t off = static_cast<uint32_t>(slist.size());
         for (size_t q = 0; q < c.cnt; ++q) slist.push_back(static_cast<uint32_t>(gr[c.first + q]));
         const int64_t ranges = static_cast<int64_t>((n + T - 1) / T);
+        // draws the chunk's tiles add to each batch slot, added to each of
+        // its designs once (not once per tile and design)
+        std::vector<uint64_t> chunk_batch(static_cast<size_t>(B), 0);
         for (int64_t r = 0; r < ranges; ++r) {
             SharedTile st;
             st.start = begin + static_cast<uint64_t>(r) * T;
@@ -438,10 +441,12 @@ mcd_status plan_build(mcd_ctx* ctx, const mcd_problem* pr, int32_t flags, int32_
             st.batch = static_cast<uint32_t>(r % B);
             st.scen = pr->design_scen[j0];
             st.pad = 0;
-            for (size_t q = 0; q < c.cnt; ++q)
-                batch_draws[static_cast<size_t>(gr[c.first + q]) * B + st.batch] += st.n;
+            chunk_batch[st.batch] += st.n;
             stiles.push_back(st);
         }
+        for (size_t q = 0; q < c.cnt; ++q)
+            for (int bb = 0; bb < B; ++bb)
+                batch_draws[static_cast<size_t>(gr[c.first + q]) * B + bb] += chunk_batch[static_cast<size_t>(bb)];
     }
     if (static_cast<int64_t>(stiles.size()) + total_tiles >= (1ll << 31))
         return fail(ctx, MCD_EINVAL, "too many tiles (reduce n_draws)");
