@@ -1,17 +1,17 @@
 // Instruction-throughput microbenchmarks: the issue rate of each instruction
 // class the sampling kernels are built from (32x32->64 multiply, three-input
 // logic, FP32 FMA, each MUFU function, broadcast shared-memory loads), in
-// operations per SM clock.  Together
-// with the per-draw operation counts of the estimator they give the
-// min-over-pipes bound on draw-evaluations per second.
+// operations per SM clock.  Together with the per-draw operation counts of
+// the estimator they give the min-over-pipes bound on draw-evaluations per
+// second.
 //
-// Each thread runs eight independent dependency chains of the measured
-// instruction (written in inline PTX, so the class is fixed), enough warps are
-// resident that latency is hidden (8 blocks of 256 threads per SM), and every
-// block reads the SM's cycle counter after a barrier on both sides of the
-// loop.  Operations per SM clock = (the blocks' operations on one SM) /
-// (last end - first start on that SM), a figure that does not depend on the
-// clock frequency.
+// Each thread runs independent dependency chains of the measured instruction
+// (eight; four for the shared loads, two Philox states), written in inline
+// PTX so that the class is fixed.  Enough warps are resident to hide latency
+// (8 blocks of 256 threads per SM), and every block reads the SM's cycle
+// counter after a barrier on both sides of the loop.  Operations per SM
+// clock = (the blocks' operations on one SM) / (last end - first start on
+// that SM), a figure that does not depend on the clock frequency.
 #include <cstdint>
 
 #include <cuda_runtime.h>
