@@ -318,6 +318,13 @@ mcd_status mcd_debug_normals(mcd_ctx* ctx, uint64_t seed, uint64_t key, uint64_t
                              uint64_t count, float* z32, double* z64, uint32_t* words,
                              mcd_stream stream);
 
+/* Host-side fault injection for tests of error handling: the next launch
+ * of any plan of this context (mcd_plan_eval, mcd_plan_grad, the one-shot
+ * calls) queues no GPU work and returns MCD_ECUDA, with the text of CUDA
+ * error `cuda_error` and "injected" in mcd_last_error().  0 clears a pending
+ * injection.  Nothing reaches the GPU, so the context stays usable. */
+mcd_status mcd_debug_fail_next(mcd_ctx* ctx, int32_t cuda_error);
+
 /* ---- measurement --------------------------------------------------------- */
 
 /* Instruction classes of the sampling kernels, for mcd_pipe_rate. */

@@ -76,6 +76,7 @@ def load(path=LIB_PATH):
         "mcd_debug_normals": (i32, [vp, u64, u64, u64, u64, vp, vp, vp, vp]),
         "mc_design_eval_noalloc": (i32, [ctypes.c_int, ctypes.POINTER(CProblem), u64, vp, vp, vp, vp]),
         "mcd_pipe_rate": (i32, [vp, i32, i32, ctypes.POINTER(f64), vp]),
+        "mcd_debug_fail_next": (i32, [vp, i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -123,6 +124,11 @@ class Context:
     def sync_status(self, stream=None):
         """Wait for the stream and raise on a device-side error (non-SPD, NaN)."""
         self.check(self.lib.mcd_sync_status(self.handle, _stream(stream)))
+
+    def fail_next_launch(self, cuda_error):
+        """Host-side fault injection (mcd_debug_fail_next): the next plan
+        launch on this context returns MCD_ECUDA without queuing work."""
+        self.check(self.lib.mcd_debug_fail_next(self.handle, int(cuda_error)))
 
     def close(self):
         if getattr(self, "handle", None):

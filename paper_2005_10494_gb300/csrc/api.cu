@@ -91,6 +91,7 @@ struct mcd_ctx {
     DevStatus* d_status = nullptr;
     std::map<TuneKey, LaunchCfg> tuned;
     std::mutex mu;
+    int inject = 0;                  // mcd_debug_fail_next: CUDA error of the next plan launch
 };
 
 struct mcd_plan {
@@ -554,6 +555,18 @@ struct LaunchArgs {
 
 // The whole launch sequence of one evaluation on `stream`.
 mcd_status enqueue(mcd_plan* pl, const LaunchArgs& a, cudaStream_t stream) {
+    {
+        // host-side fault injection: report the chosen CUDA error, queue nothing
+        mcd_ctx* c = pl->ctx;
+        std::lock_guard<std::mutex> lk(c->mu);
+        if (c->inject != 0) {
+            const cudaError_t e = static_cast<cudaError_t>(c->inject);
+            c->inject = 0;
+            c->err = std::string("launch: ") + cudaGetErrorString(e) + " (injected by mcd_debug_fail_next)";
+            c->err_index = -1;
+            return MCD_ECUDA;
+        }
+    }
     mcd_ctx* ctx = pl->ctx;
     if (a.grad && (pl->k > 0) != (a.jac != nullptr))
         return fail(ctx, MCD_EINVAL, "the Jacobian must be given exactly when the plan has k > 0");
@@ -1153,6 +1166,14 @@ mcd_status mcd_debug_normals(mcd_ctx* ctx, uint64_t seed, uint64_t key, uint64_t
     MCD_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
     MCD_CUDA(launch_debug_normals(seed, key, m_begin, count, z32, z64, words, reinterpret_cast<cudaStream_t>(stream)),
              "debug launch");
+    return MCD_OK;
+}
+
+mcd_status mcd_debug_fail_next(mcd_ctx* ctx, int32_t cuda_error) {
+    if (!ctx) return MCD_EINVAL;
+    if (cuda_error < 0) return fail(ctx, MCD_EINVAL, "cuda_error must be >= 0");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->inject = cuda_error;
     return MCD_OK;
 }
 

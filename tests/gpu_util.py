@@ -46,8 +46,9 @@ def oracle_same_stream(prob, seed, idx, eps=EPS32, grad=False, h=0.0):
 
 
 def report(name, **stats):
-    """Append one JSON line of parity statistics to the file named by the
-    environment variable MCD_PARITY_REPORT (nothing when it is unset)."""
+    """Append one JSON line of parity statistics (with the per-design records
+    of the check) to the file named by the environment variable
+    MCD_PARITY_REPORT (nothing when it is unset)."""
     import json
     import os
     path = os.environ.get("MCD_PARITY_REPORT")
@@ -58,17 +59,20 @@ def report(name, **stats):
 
 def assert_discordance(gpu_hits, ora, idx):
     """|hits_gpu - hits_oracle| <= ambiguous draws, design by design.
-    Returns (designs, total |difference|, total ambiguous draws)."""
-    bad = []
+    Returns the number of designs, the total |difference| and ambiguous
+    draws, and per design its counts."""
+    bad, rec = [], []
     tot_diff = tot_amb = 0
     for k, j in enumerate(idx):
         diff = abs(int(gpu_hits[j]) - int(ora["hits"][k]))
         tot_diff += diff
         tot_amb += int(ora["ambiguous"][k])
+        rec.append({"design": int(j), "hits_gpu": int(gpu_hits[j]), "hits_oracle": int(ora["hits"][k]),
+                    "ambiguous": int(ora["ambiguous"][k])})
         if diff > int(ora["ambiguous"][k]):
             bad.append((j, int(gpu_hits[j]), int(ora["hits"][k]), int(ora["ambiguous"][k])))
     assert not bad, "designs outside the same-stream band: %r" % bad[:10]
-    return {"designs": len(idx), "hit_difference": tot_diff, "ambiguous_draws": tot_amb}
+    return {"designs": len(idx), "hit_difference": tot_diff, "ambiguous_draws": tot_amb, "per_design": rec}
 
 
 def band(p_exact, n):
@@ -76,14 +80,19 @@ def band(p_exact, n):
 
 
 def assert_band(p_gpu, p_exact, n, idx):
-    """|p_gpu - p_exact| <= 5 SE + 1e-7 per design.  Returns (designs, the
-    largest and the mean |error| in units of SE)."""
+    """|p_gpu - p_exact| <= 5 SE + 1e-7 per design.  Returns the number of
+    designs, the largest and the mean |error| in units of SE, and per design
+    p_gpu, p_exact, n and the signed error in SE."""
     bad = [(j, float(p_gpu[j]), float(p_exact[k])) for k, j in enumerate(idx)
            if abs(p_gpu[j] - p_exact[k]) > band(p_exact[k], n if np.isscalar(n) else n[k])]
     assert not bad, "designs outside 5 SE of the exact value: %r" % bad[:10]
-    z = []
+    z, rec = [], []
     for k, j in enumerate(idx):
         nn = n if np.isscalar(n) else n[k]
         se = math.sqrt(max(p_exact[k] * (1.0 - p_exact[k]), 1e-300) / nn)
-        z.append(abs(float(p_gpu[j]) - float(p_exact[k])) / se)
-    return {"designs": len(idx), "max_abs_z": max(z) if z else 0.0, "mean_abs_z": float(np.mean(z)) if z else 0.0}
+        zk = (float(p_gpu[j]) - float(p_exact[k])) / se
+        z.append(abs(zk))
+        rec.append({"design": int(j), "p_gpu": float(p_gpu[j]), "p_exact": float(p_exact[k]), "n": int(nn),
+                    "z": zk})
+    return {"designs": len(idx), "max_abs_z": max(z) if z else 0.0, "mean_abs_z": float(np.mean(z)) if z else 0.0,
+            "per_design": rec}

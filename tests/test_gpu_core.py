@@ -122,6 +122,41 @@ def test_one_shot_equals_plan(ctx):
     np.testing.assert_array_equal(one["hits"].cpu().numpy(), plan["hits"])
 
 
+def test_injected_launch_failure(ctx):
+    """Host-side fault injection (no GPU fault): the next launch returns
+    MCD_ECUDA with the injected error's text and queues nothing; the plan,
+    the one-shot call and the context stay usable and give the same counts."""
+    import torch
+
+    import paper_2005_10494_gb300 as pkg
+    from paper_2005_10494_gb300.binding import MCD_ECUDA, MCD_EINVAL
+    prob = workloads.c1(n_draws=5000, keys="independent")
+    dp = pkg.DeviceProblem.from_workload(prob)
+    plan = pkg.Plan(ctx, dp, graph=False)
+    ref = plan.eval(4)["hits"].clone()
+    ctx.sync_status()
+    ctx.fail_next_launch(9)
+    with pytest.raises(pkg.MCDError) as e:
+        plan.eval(4)
+    assert e.value.code == MCD_ECUDA and "injected" in str(e.value)
+    assert torch.equal(plan.eval(4)["hits"], ref)
+    ctx.sync_status()
+    ctx.fail_next_launch(2)
+    with pytest.raises(pkg.MCDError) as e:
+        pkg.mc_design_eval(ctx, dp, 4)
+    assert e.value.code == MCD_ECUDA
+    assert torch.equal(pkg.mc_design_eval(ctx, dp, 4)["hits"], ref)
+    ctx.sync_status()
+    ctx.fail_next_launch(9)
+    ctx.fail_next_launch(0)            # cleared before any launch
+    assert torch.equal(plan.eval(4)["hits"], ref)
+    ctx.sync_status()
+    with pytest.raises(pkg.MCDError) as e:
+        ctx.fail_next_launch(-1)
+    assert e.value.code == MCD_EINVAL
+    plan.close()
+
+
 # ------------------------------------------------- uneven / ragged problems
 @pytest.mark.parametrize("seed", [0, 1, 2, 3])
 def test_random_problems_same_stream(ctx, seed):
