@@ -173,14 +173,15 @@ __global__ void __launch_bounds__(kNb * kNb) chol_diag_kernel(double* __restrict
     const double floor_p = static_cast<double>(n) * 2.220446049250313e-16 * __longlong_as_double(static_cast<long long>(*amax));
     if (ty < b && tx < b) a[ty][tx] = G[static_cast<int64_t>(ty) * ld + tx];
     __syncthreads();
+    __shared__ double inv;
     for (int kk = 0; kk < b; ++kk) {
         if (threadIdx.x == 0) {
             const double p = a[kk][kk];
-            if (!(p > floor_p)) { *bad = 1; a[kk][kk] = 1.0; }
-            else a[kk][kk] = sqrt(p);
+            if (!(p > floor_p)) { *bad = 1; a[kk][kk] = 1.0; inv = 1.0; }
+            else { const double r = sqrt(p); a[kk][kk] = r; inv = 1.0 / r; }
         }
         __syncthreads();
-        if (tx == kk && ty > kk && ty < b) a[ty][kk] /= a[kk][kk];
+        if (tx == kk && ty > kk && ty < b) a[ty][kk] *= inv;
         __syncthreads();
         if (ty > kk && tx > kk && tx <= ty && ty < b) a[ty][tx] -= a[ty][kk] * a[tx][kk];
         __syncthreads();
@@ -263,7 +264,10 @@ constexpr int kSolveThreads = 1024;
 __global__ void __launch_bounds__(kSolveThreads) chol_solve_kernel(const double* __restrict__ L, int64_t ld, int n,
                                                                   double* __restrict__ z) {
     __shared__ double part[32];
+    extern __shared__ double dinv[];                          // 1 / L_ii, n entries
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dinv[i] = 1.0 / L[static_cast<int64_t>(i) * ld + i];
+    __syncthreads();
     for (int i0 = 0; i0 < n; i0 += 32) {
         const int b = n - i0 < 32 ? n - i0 : 32;
         if (warp < b) {
@@ -280,7 +284,7 @@ __global__ void __launch_bounds__(kSolveThreads) chol_solve_kernel(const double*
                 const double lrc = lane < r ? L[static_cast<int64_t>(i0 + r) * ld + i0 + lane] : 0.0;
                 double t = lrc * zc;
                 for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-                const double zr = (part[r] - t) / L[static_cast<int64_t>(i0 + r) * ld + i0 + r];
+                const double zr = (part[r] - t) * dinv[i0 + r];
                 if (lane == r) zc = zr;
             }
             if (lane < b) z[i0 + lane] = zc;
@@ -297,7 +301,7 @@ __global__ void __launch_bounds__(kSolveThreads) chol_solve_kernel(const double*
                 const double lcr = (lane > r && lane < b) ? L[static_cast<int64_t>(i0 + lane) * ld + i0 + r] : 0.0;
                 double t = lcr * wc;
                 for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-                const double wr = (z[i0 + r] - t) / L[static_cast<int64_t>(i0 + r) * ld + i0 + r];
+                const double wr = (z[i0 + r] - t) * dinv[i0 + r];
                 if (lane == r) wc = wr;
             }
             if (lane < b) z[i0 + lane] = wc;
@@ -310,6 +314,17 @@ __global__ void __launch_bounds__(kSolveThreads) chol_solve_kernel(const double*
         }
         __syncthreads();
     }
+}
+
+// The two triangular solves with L (n <= 16384: the reciprocals of the
+// diagonal, 8 n bytes, in dynamic shared memory).
+cudaError_t launch_solve(const double* L, int64_t ld, int n, double* z, cudaStream_t stream) {
+    const size_t smem = sizeof(double) * static_cast<size_t>(n);
+    cudaError_t e = cudaFuncSetAttribute(chol_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    chol_solve_kernel<<<1, kSolveThreads, smem, stream>>>(L, ld, n, z);
+    return cudaGetLastError();
 }
 
 // c = Q [0; w], R d = y~_1 - B12 w, fitted = y - s c; NaN when the
@@ -645,7 +660,7 @@ cudaError_t tps_fit_one(const double* x, const double* y, int N, int k, double s
     chol_blocked(B, N, n, amax, bad, stream);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(z, yt + m, sizeof(double) * n, cudaMemcpyDeviceToDevice, stream)) != cudaSuccess) return e;
-    chol_solve_kernel<<<1, kSolveThreads, 0, stream>>>(B, N, n, z);
+    if ((e = launch_solve(B, N, n, z, stream)) != cudaSuccess) return e;
     combine_kernel<<<1, 1024, 0, stream>>>(A, V, tau, R, yt, z, y, N, k, s, bad, coef, fitted, status, surf);
     return cudaGetLastError();
 }
@@ -692,7 +707,7 @@ cudaError_t tps_gcv(const double* x, const double* y, int N, int k, const double
         chol_blocked(W, n, n, amax, bad, stream);
         if ((e = cudaMemcpyAsync(z, yt + m, sizeof(double) * n, cudaMemcpyDeviceToDevice, stream)) != cudaSuccess)
             return e;
-        chol_solve_kernel<<<1, kSolveThreads, 0, stream>>>(W, n, n, z);
+        if ((e = launch_solve(W, n, n, z, stream)) != cudaSuccess) return e;
         tri_inv_diag_kernel<<<nb, kNb, 0, stream>>>(W, X, n);
         for (int bi = 1; bi < nb; ++bi) tri_inv_step_kernel<<<bi, 256, 0, stream>>>(W, X, n, bi);
         sumsq_lower_kernel<<<n, 128, 0, stream>>>(X, n, trace);
