@@ -61,3 +61,22 @@ def test_alpha_optimisation_with_gcv_smoothing(ctx):
     assert 1e-10 <= res["smoothing"] <= 1e-2
     p_star = exact_power("c", PAPER_R_C, res["alpha"])
     assert p_star >= exact_power("c", PAPER_R_C, PAPER_ALPHA_C) - 2e-4, (res["alpha"], p_star, res["smoothing"])
+
+
+@pytest.mark.parametrize("cond", ["a", "b"])
+def test_choice_of_nested_populations_other_conditions(ctx, cond):
+    """Conditions (a) and (b) of the Sec. 3 sweep through the same search, on
+    every 4th of the 171 pairs with fewer splits and draws: a valid r, an
+    allocation that meets Eq. 2 to Monte Carlo precision (the final
+    calibration uses the search's 1e6 draws per round), and a spline maximum
+    that estimates the exact power of the design it returns."""
+    from paper_2005_10494_gb300 import search
+    pairs = workloads.paper_r_pairs()[::4]
+    out = search.optimise_design(ctx, cond, r_pairs=pairs, n3=400, n_draws=1_000_000, seed=5)
+    r, alpha = out["r"], np.asarray(out["alpha"])
+    assert 1.0 > r[1] > r[2] > 0.0
+    assert np.all(alpha > 0)
+    _, _, Sig0 = workloads.paper_law(cond, r)
+    fwer = quad.fwer(quad.norm_ppf(1.0 - alpha), Sig0)
+    assert abs(fwer - workloads.ALPHA0) <= 5 * np.sqrt(0.025 * 0.975 / 1e6) + 1e-7, (r, alpha, fwer)
+    assert abs(out["p_fit"] - exact_power(cond, r, alpha)) <= 5e-3, (r, alpha, out["p_fit"])
