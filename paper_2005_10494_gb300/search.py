@@ -155,9 +155,10 @@ def optimise_design(ctx, cond, r_pairs=None, n3=2000, n_draws=10_000_000, seed=0
     (default the paper's 171 pairs), a thin-plate spline of the optimal power
     over (r2, r3 / r2), its maximiser within two grid steps of the best
     evaluated pair (the search starts from the best point, as Sec. 2.3 does
-    for alpha; the box stays inside the range of the evaluated pairs, so
-    1 > r2 > r3 > 0 holds and the spline is not extrapolated into regions
-    without data), and optimise_alpha at the maximiser.  Returns dict r,
+    for alpha; the box stays inside the range of the evaluated pairs and
+    keeps r3 at or above the smallest evaluated r3, so 1 > r2 > r3 > 0 holds
+    and the spline is not extrapolated into regions without data), and
+    optimise_alpha at the maximiser.  Returns dict r,
     alpha, p_fit, per_r (list of (r2, r3, p_fit))."""
     import torch
 
@@ -176,8 +177,14 @@ def optimise_design(ctx, cond, r_pairs=None, n3=2000, n_draws=10_000_000, seed=0
     ib = int(np.argmax(vals))
     step = float(np.min(np.diff(np.unique(pts[:, 0])))) if len(np.unique(pts[:, 0])) > 1 else 0.05
     reach = np.array([2.0 * step, 2.0 * step / pts[ib, 0]])
-    lo = _dev(np.maximum(pts.min(0), pts[ib] - reach), dev)
-    hi = _dev(np.minimum(pts.max(0), pts[ib] + reach), dev)
+    lo_np = np.maximum(pts.min(0), pts[ib] - reach)
+    hi_np = np.minimum(pts.max(0), pts[ib] + reach)
+    # r3 = r2 * (r3 / r2) stays at or above the smallest evaluated r3: a
+    # rectangle in these coordinates would otherwise reach below it (small
+    # r2 with the smallest ratio), where the spline has no data
+    r3_min = min(b for _, b, _ in per_r)
+    lo_np[1] = min(max(lo_np[1], r3_min / lo_np[0]), hi_np[1])
+    lo, hi = _dev(lo_np, dev), _dev(hi_np, dev)
     am = binding.mc_tps_argmax(ctx, x, fit, lo, hi, iters=300)
     ctx.sync_status()
     r2s, v = am["x"].cpu().numpy()[0]
