@@ -151,6 +151,27 @@ def optimise_alpha(ctx, cond, r, n3=2000, n_draws=10_000_000, seed=0, smoothing=
             "p_hat": p_hat.cpu().numpy(), "smoothing": smoothing}
 
 
+def r_search_box(per_r):
+    """Spline coordinates and search box of the choice of r (host only).
+
+    per_r: list of (r2, r3, optimal power).  Returns the points (r2, r3/r2),
+    their values, and the box lo, hi: within two grid steps of the best
+    pair, inside the range of the evaluated points, and with r3 = r2 * (r3/r2)
+    at or above the smallest evaluated r3 (a rectangle in these coordinates
+    would otherwise reach below it at small r2 with the smallest ratio,
+    where the spline has no data)."""
+    pts = np.array([[a, b / a] for a, b, _ in per_r])
+    vals = np.array([v for _, _, v in per_r])
+    ib = int(np.argmax(vals))
+    step = float(np.min(np.diff(np.unique(pts[:, 0])))) if len(np.unique(pts[:, 0])) > 1 else 0.05
+    reach = np.array([2.0 * step, 2.0 * step / pts[ib, 0]])
+    lo = np.maximum(pts.min(0), pts[ib] - reach)
+    hi = np.minimum(pts.max(0), pts[ib] + reach)
+    r3_min = min(b for _, b, _ in per_r)
+    lo[1] = min(max(lo[1], r3_min / lo[0]), hi[1])
+    return pts, vals, lo, hi
+
+
 def optimise_design(ctx, cond, r_pairs=None, n3=2000, n_draws=10_000_000, seed=0, smoothing=1e-6,
                     r_smoothing=1e-6):
     """The choice of nested populations for n = 3 (Sec. 2.4 with power as
@@ -173,20 +194,9 @@ def optimise_design(ctx, cond, r_pairs=None, n3=2000, n_draws=10_000_000, seed=0
                              smoothing=smoothing, final_draws=n_draws)
         per_r.append((r2, r3, res["p_fit"]))
     dev = torch.device("cuda", ctx.device)
-    pts = np.array([[a, b / a] for a, b, _ in per_r])
-    vals = np.array([v for _, _, v in per_r])
+    pts, vals, lo_np, hi_np = r_search_box(per_r)
     x = _dev(pts, dev).reshape(1, len(per_r), 2)
     fit = binding.mc_tps_fit(ctx, x, _dev(vals, dev).reshape(1, -1), smoothing=r_smoothing)
-    ib = int(np.argmax(vals))
-    step = float(np.min(np.diff(np.unique(pts[:, 0])))) if len(np.unique(pts[:, 0])) > 1 else 0.05
-    reach = np.array([2.0 * step, 2.0 * step / pts[ib, 0]])
-    lo_np = np.maximum(pts.min(0), pts[ib] - reach)
-    hi_np = np.minimum(pts.max(0), pts[ib] + reach)
-    # r3 = r2 * (r3 / r2) stays at or above the smallest evaluated r3: a
-    # rectangle in these coordinates would otherwise reach below it (small
-    # r2 with the smallest ratio), where the spline has no data
-    r3_min = min(b for _, b, _ in per_r)
-    lo_np[1] = min(max(lo_np[1], r3_min / lo_np[0]), hi_np[1])
     lo, hi = _dev(lo_np, dev), _dev(hi_np, dev)
     am = binding.mc_tps_argmax(ctx, x, fit, lo, hi, iters=300)
     ctx.sync_status()
