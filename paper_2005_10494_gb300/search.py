@@ -106,7 +106,8 @@ def optimise_alpha(ctx, cond, r, n3=2000, n_draws=10_000_000, seed=0, smoothing=
     splits), a thin-plate spline with `smoothing` (a value, or "gcv": the
     minimiser of the GCV score over 1e-10 .. 1e-2) is fitted over u and
     maximised in the box, and the split at the maximiser is calibrated once
-    more with final_draws.  Eight calibration rounds leave |FWER - alpha0|
+    more with final_draws (skipped when final_draws is 0: alpha and scale
+    are then None).  Eight calibration rounds leave |FWER - alpha0|
     at the returned scale near 1e-6, a few per cent of the estimate's own
     Monte Carlo error at 1e7 draws; 14 rounds give the same scales to four
     digits.  Returns dict u, alpha, p_fit (the spline's maximum), p_hat
@@ -141,12 +142,16 @@ def optimise_alpha(ctx, cond, r, n3=2000, n_draws=10_000_000, seed=0, smoothing=
     ctx.sync_status()
     u_star = am["x"].cpu().numpy()[0]
     w_star = workloads.split_from_box(u_star)[0]
+    plan.close()
+    if not final_draws:
+        # the caller needs only the spline's maximum (the loop over r)
+        return {"u": u_star, "alpha": None, "scale": None, "p_fit": float(am["f"].item()),
+                "p_hat": p_hat.cpu().numpy(), "smoothing": smoothing}
     one = binding.DeviceProblem([n], [0], [final_draws], [2], _dev(Sig0.ravel(), dev), _dev(np.zeros(n), dev),
                                 _dev(np.zeros(n), dev))
     c1 = binding.mc_fwer_calibrate(ctx, one, _dev(w_star, dev), workloads.ALPHA0, rounds=rounds, seed=seed + 2)
     ctx.sync_status()
     scale = float(c1["scale"].item())
-    plan.close()
     return {"u": u_star, "alpha": scale * w_star, "scale": scale, "p_fit": float(am["f"].item()),
             "p_hat": p_hat.cpu().numpy(), "smoothing": smoothing}
 
@@ -191,7 +196,7 @@ def optimise_design(ctx, cond, r_pairs=None, n3=2000, n_draws=10_000_000, seed=0
     per_r = []
     for q, (r2, r3) in enumerate(pairs):
         res = optimise_alpha(ctx, cond, (1.0, r2, r3), n3=n3, n_draws=n_draws, seed=seed + 7 * q,
-                             smoothing=smoothing, final_draws=n_draws)
+                             smoothing=smoothing, final_draws=0)
         per_r.append((r2, r3, res["p_fit"]))
     dev = torch.device("cuda", ctx.device)
     pts, vals, lo_np, hi_np = r_search_box(per_r)
