@@ -1,5 +1,5 @@
 """The d=10 configuration's design search: gradient ascent driven by the
-adjoint against grid + local-quadratic smoothing + argmax, both judged by the
+adjoint against grid + local-quadratic smoothing + argmax, both evaluated by the
 exact objective (AR(1) Markov-recursion quadrature)."""
 import numpy as np
 import pytest
