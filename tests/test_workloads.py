@@ -107,3 +107,41 @@ def test_paper_designs_match_oracle_collapse():
         mu, C = design.collapsed_prior(r, I3s[j], d0s[j](r))
         np.testing.assert_allclose(p.mus[j], mu, rtol=1e-14, atol=0)
         np.testing.assert_allclose(p.sigmas[j], C, rtol=1e-14, atol=1e-15)
+
+
+def test_split_from_box_maps_the_box_onto_the_simplex():
+    """w_1 = u_1, w_j = u_j prod_{l<j} (1 - u_l), w_n = prod (1 - u_l): every
+    box point gives a split on the simplex, the corners give its vertices,
+    and the map is inverted by u_j = w_j / (1 - w_1 - ... - w_{j-1})."""
+    rng = np.random.default_rng(0)
+    for n in (2, 3, 5):
+        u = rng.uniform(0.0, 1.0, (500, n - 1))
+        w = workloads.split_from_box(u)
+        assert w.shape == (500, n)
+        assert np.all(w >= 0.0)
+        np.testing.assert_allclose(w.sum(1), 1.0, rtol=0, atol=1e-14)
+        rest = 1.0 - np.concatenate([np.zeros((500, 1)), np.cumsum(w[:, :-1], 1)], 1)
+        np.testing.assert_allclose(w[:, :-1] / rest[:, :-1], u, rtol=1e-12, atol=1e-12)
+    np.testing.assert_array_equal(workloads.split_from_box([[1.0, 0.3]]), [[1.0, 0.0, 0.0]])
+    np.testing.assert_array_equal(workloads.split_from_box([[0.0, 1.0]]), [[0.0, 1.0, 0.0]])
+    np.testing.assert_array_equal(workloads.split_from_box([[0.0, 0.0]]), [[0.0, 0.0, 1.0]])
+
+
+def test_paper_r_pairs_are_the_171_nested_pairs():
+    pairs = workloads.paper_r_pairs()
+    assert len(pairs) == 171 == 19 * 18 // 2
+    assert len(set(pairs)) == 171
+    for r2, r3 in pairs:
+        assert 0.0 < r3 < r2 < 1.0
+        for v in (r2, r3):
+            assert abs(v / 0.05 - round(v / 0.05)) < 1e-9
+    assert min(b for _, b in pairs) == 0.05 and max(a for a, _ in pairs) == 0.95
+
+
+def test_box_points_are_seeded_and_uniform():
+    a = workloads.box_points(20000, 2, seed=3)
+    np.testing.assert_array_equal(a, workloads.box_points(20000, 2, seed=3))
+    assert not np.array_equal(a, workloads.box_points(20000, 2, seed=4))
+    assert np.all((a >= 0.0) & (a <= 1.0))
+    np.testing.assert_allclose(a.mean(0), 0.5, atol=0.01)
+    np.testing.assert_allclose(a.var(0), 1.0 / 12.0, atol=0.003)
