@@ -90,3 +90,19 @@ def test_binding_constants_match_the_header():
     for name in ["MCD_PLAN_GRAD", "MCD_PLAN_AUTOTUNE", "MCD_PLAN_GRAPH", "MCD_PLAN_FP64", "MCD_PLAN_TIMING",
                  "MCD_PLAN_SHARED", "MCD_SHARED_MIN", "MCD_MAX_D", "MCD_ANY_EXCEEDS", "MCD_ALL_BELOW"]:
         assert name in defs and hasattr(b, name), name
+
+
+def test_pipe_classes_match_the_header():
+    """binding.PIPE_CLASSES lists the MCD_PIPE_* classes in header order, and
+    bench.py's per-draw counts use only measured classes."""
+    import bench
+    import paper_2005_10494_gb300.binding as b
+    text = open(HEADER).read()
+    defs = {k: int(v) for k, v in re.findall(r"^#define\s+MCD_PIPE_(\w+)\s+(\d+)", text, re.M)}
+    count = defs.pop("COUNT")
+    assert sorted(defs.values()) == list(range(count))
+    assert len(b.PIPE_CLASSES) == count
+    for name, idx in defs.items():
+        assert b.PIPE_CLASSES[idx] == name.lower(), (name, idx)
+    used = set(bench.class_counts(3, True)) | {"philox"}
+    assert used <= set(b.PIPE_CLASSES) | {"alu", "ffma"}
