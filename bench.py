@@ -8,9 +8,15 @@ in the same pass), the FP64 finalisation (p, SE, gradients w.r.t. cutoff,
 allocation, delta+, delta-) and the local-quadratic smoothing with argmax.
 
 Prints one JSON line.  `value` is draw-evaluations per second over the whole
-job (all ranks); `roofline` refers to the sampling kernel; `e2e` times the
-same step through the public API with inputs copied from pinned host memory
-and results copied back; `cpu_baseline` times the FP64 oracle on the host.
+job (all ranks); `roofline` refers to the sampling kernel (issue slots of
+its algorithmic operations) and `pipe_bound` to the min-over-pipes bound
+from the instruction-class rates this GPU measures (`mcd_pipe_rate`); `e2e`
+times the same step through the public API with inputs copied from pinned
+host memory and results copied back; `cpu_baseline` times the FP64 oracle
+on the host and compares its hit counts with the GPU's at the same seed.
+`extras` holds the other configurations (d = 10, 20, the batched uneven
+problem, shared draws, FP64 path, smoothing at scale) and the paper's own
+workloads (two-layer estimator, FWER calibration, the Sec. 3 sweep).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -32,7 +38,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MC draw-evals/s & % FP32-pipe peak at d=3/10/20; adjoint overhead vs plain"
 UNIT = "draw-evals/s"
-SM_COUNT_NOMINAL = 152
 LANES = 128
 SM_MAX_MHZ = 2070.0
 WORKLOAD = ("d=3 design grid: 16 scenarios x 64 cutoff quantiles x 64 allocation fractions, "
