@@ -127,6 +127,8 @@ mcd_status mcd_sync_status(mcd_ctx* ctx, mcd_stream stream);
  * (1..8), or 0 for gradients with respect to mu. */
 mcd_status mcd_plan_create(mcd_ctx* ctx, const mcd_problem* prob, int32_t flags,
                            int32_t k, mcd_plan** plan);
+/* Free a plan.  It may be called before or after mcd_destroy of its context
+ * (the plan keeps its own device index), but not while its work runs. */
 void       mcd_plan_destroy(mcd_plan* plan);
 
 /* Estimate p for every design (Sec. 2.2, Eq. 7 with independent draws).

@@ -96,6 +96,7 @@ struct mcd_ctx {
 
 struct mcd_plan {
     mcd_ctx* ctx = nullptr;
+    int device = 0;                  // the context's GPU: destroy must not read *ctx (it may be gone)
     bool stream_ordered = false;     // one-shot plan: allocations on a stream
     cudaStream_t alloc_stream = nullptr;
     int32_t S = 0, J = 0, region = 0, k = 0, flags = 0;
@@ -254,6 +255,7 @@ mcd_status validate_problem(mcd_ctx* ctx, const mcd_problem* pr, int32_t k) {
 mcd_status plan_build(mcd_ctx* ctx, const mcd_problem* pr, int32_t flags, int32_t k, mcd_plan* pl,
                       const TileFilter& filt = TileFilter()) {
     pl->ctx = ctx;
+    pl->device = ctx->device;
     pl->S = pr->n_scen;
     pl->J = pr->n_design;
     pl->region = pr->region;
@@ -804,6 +806,7 @@ void mcd_destroy(mcd_ctx* ctx) {
     cudaSetDevice(ctx->device);
     cudaFree(ctx->d_status);
     delete ctx;
+    cudaGetLastError();              // a void call leaves no error for the next one
 }
 
 const char* mcd_last_error(const mcd_ctx* ctx) { return ctx ? ctx->err.c_str() : "context is NULL"; }
@@ -857,9 +860,12 @@ mcd_status mcd_plan_create(mcd_ctx* ctx, const mcd_problem* prob, int32_t flags,
 
 void mcd_plan_destroy(mcd_plan* plan) {
     if (!plan) return;
-    cudaSetDevice(plan->ctx->device);
+    // the plan's own device index: its context may already be destroyed
+    // (e.g. a garbage collector finalising both in either order)
+    cudaSetDevice(plan->device);
     plan_release(plan);
     delete plan;
+    cudaGetLastError();              // a void call leaves no error for the next one
 }
 
 mcd_status mcd_plan_eval(mcd_plan* plan, uint64_t seed, uint64_t* hits, double* p, double* se, mcd_stream stream) {

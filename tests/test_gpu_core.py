@@ -157,6 +157,31 @@ def test_injected_launch_failure(ctx):
     plan.close()
 
 
+def test_plan_destroyed_after_its_context(ctx):
+    """A plan may outlive its context (a garbage collector can finalise the
+    two in either order): destroying it reads nothing of the freed context
+    and leaves no CUDA error behind for the next call."""
+    import torch
+
+    import paper_2005_10494_gb300 as pkg
+    prob = workloads.c1(n_draws=5000, keys="independent")
+    dp = pkg.DeviceProblem.from_workload(prob)
+    ref = pkg.mc_design_eval(ctx, dp, 6)["hits"].clone()
+    ctx.sync_status()
+    for _ in range(3):
+        c2 = pkg.Context(0)
+        plan = pkg.Plan(c2, dp)
+        assert torch.equal(plan.eval(6)["hits"], ref)
+        c2.sync_status()
+        c2.close()                      # the context first ...
+        plan.close()                    # ... then its plan
+    x = torch.as_tensor(np.random.default_rng(0).random((1, 40, 2)), dtype=torch.float64, device="cuda")
+    y = torch.sin(x[..., 0]).contiguous()
+    pkg.mc_tps_fit(ctx, x, y, smoothing=1e-6)   # checks for launch errors
+    assert torch.equal(pkg.mc_design_eval(ctx, dp, 6)["hits"], ref)
+    ctx.sync_status()
+
+
 # ------------------------------------------------- uneven / ragged problems
 @pytest.mark.parametrize("seed", [0, 1, 2, 3])
 def test_random_problems_same_stream(ctx, seed):
