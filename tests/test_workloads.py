@@ -145,3 +145,37 @@ def test_box_points_are_seeded_and_uniform():
     assert np.all((a >= 0.0) & (a <= 1.0))
     np.testing.assert_allclose(a.mean(0), 0.5, atol=0.01)
     np.testing.assert_allclose(a.var(0), 1.0 / 12.0, atol=0.003)
+
+
+def test_nested_correlation_matches_patient_level_simulation():
+    """Eq. 1 from its construction: the Z statistic of population k is the
+    scaled sum of its patients' scores, populations are nested (the first
+    n r_k patients), so corr(Z_k, Z_l) = n_l / sqrt(n_k n_l) = sqrt(r_l / r_k).
+    Simulated at patient level; the workload's Sigma(r) and the oracle's
+    restatement (its collapsed law with a vanishing prior) both match."""
+    from oracle import design
+    r = np.array([1.0, 0.6, 0.25])
+    n = 400
+    sizes = (n * r).astype(int)
+    rng = np.random.default_rng(11)
+    eps = rng.standard_normal((40000, n))
+    cs = np.cumsum(eps, axis=1)
+    z = np.stack([cs[:, m - 1] / np.sqrt(m) for m in sizes], axis=1)
+    emp = np.corrcoef(z, rowvar=False)
+    np.testing.assert_allclose(workloads.nested_sigma(r), emp, atol=0.015)
+    _, cov = design.collapsed_prior(r, 211.0, [0.2, 0.2, 0.2], prior_sd_scale=1e14)
+    np.testing.assert_allclose(cov, workloads.nested_sigma(r), rtol=0, atol=1e-9)
+    np.testing.assert_allclose(np.diag(emp), 1.0)
+
+
+def test_collapsed_prior_covariance_closed_form():
+    """With the prior of Eq. 10, sd_i = 1 / sqrt(20 r_i) and prior
+    correlation Sigma(r), S_i sd_i = sqrt(I3 / 20) for every population, so
+    the folded covariance is Sigma(r) (1 + I3 / 20) and the mean S theta."""
+    from oracle import design
+    r = np.array([1.0, 0.446, 0.168])
+    d0 = np.array([0.2, 0.3, 0.5])
+    for I3 in (127.0, 211.0):
+        mean, cov = design.collapsed_prior(r, I3, d0)
+        np.testing.assert_allclose(cov, workloads.nested_sigma(r) * (1.0 + I3 / 20.0), rtol=1e-13)
+        np.testing.assert_allclose(mean, np.sqrt(r * I3) * -np.log1p(-d0), rtol=1e-14)
