@@ -90,3 +90,14 @@ def test_clock_summary():
     assert c["reasons"] == ["sw_power_cap"]
     assert c["samples"] == 3
     assert bench.ClockSampler.summarise([])["sm_mhz"] is None
+
+
+def test_hbm_peak_reads_the_measured_figure_or_falls_back(tmp_path):
+    f = tmp_path / "peaks.json"
+    f.write_text('{"hbm_gbs": 6790.0, "bf16_tflops": 1979.2}')
+    assert bench.hbm_peak(str(f)) == (6790.0, "measured (MEASURED_PEAKS.json hbm_gbs)")
+    f.write_text("not json")
+    assert bench.hbm_peak(str(f))[0] == 6800.0
+    f.write_text('{"bf16_tflops": 1979.2}')
+    assert bench.hbm_peak(str(f))[0] == 6800.0
+    assert bench.hbm_peak(str(tmp_path / "missing.json"))[0] == 6800.0
