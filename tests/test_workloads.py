@@ -179,3 +179,24 @@ def test_collapsed_prior_covariance_closed_form():
         mean, cov = design.collapsed_prior(r, I3, d0)
         np.testing.assert_allclose(cov, workloads.nested_sigma(r) * (1.0 + I3 / 20.0), rtol=1e-13)
         np.testing.assert_allclose(mean, np.sqrt(r * I3) * -np.log1p(-d0), rtol=1e-14)
+
+
+@pytest.mark.parametrize("d,eta", [(3, 1.0), (4, 2.0), (6, 2.0)])
+def test_lkj_cvine_off_diagonal_marginal(d, eta):
+    """Lewandowski, Kurowicka and Joe (2009): under LKJ(eta) in dimension d
+    every off-diagonal correlation is marginally Beta(b, b) on (-1, 1) with
+    b = eta - 1 + d / 2, whose variance is 1 / (2 b + 1)."""
+    from scipy import stats
+    rng = np.random.default_rng(17)
+    b = eta - 1.0 + d / 2.0
+    mats = [workloads.lkj_cvine(d, eta, rng) for _ in range(3000)]
+    for M in mats[:50]:
+        np.testing.assert_allclose(M, M.T)
+        np.testing.assert_allclose(np.diag(M), 1.0)
+        assert np.linalg.eigvalsh(M).min() > 0
+    iu = np.triu_indices(d, 1)
+    for i, j in zip(*iu):
+        x = np.array([M[i, j] for M in mats])
+        res = stats.kstest((x + 1.0) / 2.0, stats.beta(b, b).cdf)
+        assert res.pvalue > 1e-3, (d, eta, i, j, res)
+        assert abs(x.var() - 1.0 / (2 * b + 1)) < 0.1 / (2 * b + 1)
