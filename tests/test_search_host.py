@@ -34,3 +34,11 @@ def test_box_keeps_r3_above_the_smallest_evaluated_r3():
         for r2 in (lo[0], hi[0]):
             for v in (lo[1], hi[1]):
                 assert 1.0 > r2 > r2 * v > 0.0
+
+
+def test_box_with_one_r2_value_uses_the_default_step():
+    per_r = [(0.5, b, 1.0 - (b - 0.2) ** 2) for b in (0.05, 0.1, 0.2, 0.3, 0.4)]
+    pts, vals, lo, hi = r_search_box(per_r)
+    assert lo[0] == hi[0] == 0.5                      # the data span one r2
+    assert lo[1] <= 0.2 / 0.5 <= hi[1]
+    assert lo[0] * lo[1] >= 0.05 - 1e-12
