@@ -1,0 +1,190 @@
+"""GPU parity of the adjoint (Appendix A.3: the objective is smooth in the
+design; the derivative comes from the same sampling pass) at every dimension
+and in every kernel that computes it:
+
+* the per-dimension kernels d = 1..20 (plain, two-blocks-per-SM and
+  volatile-load instantiations), FP32 and FP64, same stream against the
+  oracle's likelihood-ratio sums A = sum 1_R z, B = sum z and sigmoid sums G;
+* the one-launch mixed-dimension kernel (d = 3..10 in one launch) on a
+  subsample of the batched uneven workload;
+* the full-size d = 10 (AR(1)) and d = 20 (block) grids against central
+  differences of the exact FP64 objective (quadrature), through the design
+  Jacobian dt/dtheta (which carries the allocation's threshold derivative).
+"""
+import concurrent.futures as cf
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import design, quad
+from oracle import mc as omc
+
+from gpu_util import EPS64, oracle_same_stream, report, run
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2005_10494_gb300 as pkg
+    return pkg.Context(0)
+
+
+def _one_scenario(d, n_designs, n_draws, seed):
+    rng = np.random.default_rng(1000 + d + 37 * seed)
+    S = workloads.lkj_cvine(d, 2.0, rng) if d > 1 else np.eye(1)
+    mus = [rng.normal(0.4, 0.5, d) for _ in range(n_designs)]
+    bs = [np.full(d, 1.6) + rng.normal(0, 0.3, d) for _ in range(n_designs)]
+    nd = [int(rng.integers(n_draws[0], n_draws[1] + 1)) for _ in range(n_designs)]
+    keys = rng.integers(0, 2 ** 40, n_designs)
+    begin = rng.integers(0, 5000, n_designs)
+    return workloads.Problem("adj-d%d" % d, [S], [0] * n_designs, mus, bs, nd, keys, draw_begin=begin)
+
+
+def _check_sums(prob, out, ora, fp64=False):
+    """grad_lr against L^-T (A - p B)/N of the oracle's sums, grad_sig against
+    G/N, design by design (k = 0: outputs packed like mu).
+
+    FP32 path: a draw whose indicator flips (an ambiguous draw, |y_i - t_i| <
+    1e-4) moves A by at most |z| <= 5.8 per coordinate and p by 1/N, and the
+    FP32 normals (error <= 1.2e-5) and sums move A and B by at most
+    2e-5 N; both are mapped through |L^-T|.  FP64 path: only the fixed-point
+    accumulation (2^-28 per tile and sum) and FP64 rounding remain."""
+    off = 0
+    worst = 0.0
+    for j in range(prob.n_design):
+        d = prob.d_of(j)
+        n = int(prob.n_draws[j])
+        S = prob.sigmas[prob.design_scen[j]]
+        g_ref = omc.lr_gradient_mu(S, ora["A"][j], ora["B"][j], ora["hits"][j], n)
+        Linv = np.linalg.inv(omc.cholesky(S))
+        amb = int(ora["ambiguous"][j])
+        amp = np.abs(Linv.T).sum(axis=1)
+        if fp64:
+            bound = amp * (1e-6 + 12.0 * amb) / n + 1e-12
+        else:
+            bound = amp * (12.0 * amb + 4.0 * n * 2e-5 + amb * np.abs(ora["B"][j]).max() / n) / n + 1e-9
+        err = np.abs(out["grad_lr"][off:off + d] - g_ref)
+        assert np.all(err <= bound), (d, j, out["grad_lr"][off:off + d], g_ref, bound)
+        worst = max(worst, float(np.max(err / bound)))
+        g_sig_ref = ora["G"][j] / n
+        if fp64:
+            np.testing.assert_allclose(out["grad_sig"][off:off + d], g_sig_ref, rtol=1e-9, atol=1e-9)
+        else:
+            np.testing.assert_allclose(out["grad_sig"][off:off + d], g_sig_ref, rtol=2e-3, atol=2e-4)
+        off += d
+    return worst
+
+
+@pytest.mark.parametrize("d", list(range(1, 21)))
+def test_gradient_sums_every_dimension(ctx, d):
+    """Each d runs alone, so the per-dimension adjoint kernel of that d is the
+    one launched (two-blocks-per-SM at 7..12, volatile factor loads at 8..12
+    and 15..19)."""
+    prob = _one_scenario(d, 3, (40_000, 70_000), 0)
+    h = 0.02
+    out = run(ctx, prob, seed=6, grad=True, k=0, h=h)
+    ora = oracle_same_stream(prob, 6, range(prob.n_design), grad=True, h=h)
+    worst = _check_sums(prob, out, ora)
+    report("adjoint sums, d=%d FP32 same stream (3 designs)" % d, designs=3, max_err_over_bound=worst)
+
+
+@pytest.mark.parametrize("d", [3, 10, 20])
+def test_gradient_sums_fp64_path(ctx, d):
+    prob = _one_scenario(d, 3, (20_000, 30_000), 1)
+    h = 0.02
+    out = run(ctx, prob, seed=7, grad=True, k=0, h=h, fp64=True)
+    ora = oracle_same_stream(prob, 7, range(prob.n_design), eps=EPS64, grad=True, h=h)
+    worst = _check_sums(prob, out, ora, fp64=True)
+    report("adjoint sums, d=%d FP64 same stream (3 designs)" % d, designs=3, max_err_over_bound=worst)
+
+
+def test_gradient_sums_mixed_dimension_launch(ctx):
+    """A subsample of the batched uneven workload (LKJ(2) scenarios, d = 3..10)
+    in one plan: its designs span several d <= 10, so the plan launches the
+    one-launch mixed-dimension adjoint kernel."""
+    prob = workloads.c3(n_scen=40)
+    rng = np.random.default_rng(8)
+    idx = []
+    for d in range(3, 11):
+        cand = [j for j in range(prob.n_design) if prob.d_of(j) == d]
+        idx += sorted(rng.choice(cand, 2, replace=False).tolist())
+    sub = prob.subset(idx)
+    sub.n_draws = rng.integers(30_000, 60_000, len(idx)).astype(np.uint64)
+    assert len(set(sub.d_of(j) for j in range(sub.n_design))) == 8
+    h = 0.01
+    out = run(ctx, sub, seed=3, grad=True, k=0, h=h)
+    ora = oracle_same_stream(sub, 3, range(sub.n_design), grad=True, h=h)
+    worst = _check_sums(sub, out, ora)
+    # the mixed launch gives the same counts as separate per-dimension launches
+    for d in range(3, 11):
+        part = [j for j in range(sub.n_design) if sub.d_of(j) == d]
+        alone = run(ctx, sub.subset(part), seed=3, grad=True, k=0, h=h)
+        np.testing.assert_array_equal(alone["hits"], out["hits"][part])
+    report("adjoint sums, mixed-dimension launch d=3..10 (16 designs)", designs=len(idx),
+           max_err_over_bound=worst)
+
+
+# ----------------------------------------------- full-size grids against FD
+def _fd_many(params_list, d, st):
+    """Central differences (step 1e-4) of the quadrature objective, one
+    process per design (spawned: a process forked after CUDA is initialised
+    must not be used)."""
+    Sigma = quad.structured_sigma(d, st)
+    ctx = mp.get_context("spawn")
+    with cf.ProcessPoolExecutor(max_workers=min(len(params_list), 16), mp_context=ctx) as ex:
+        futs = [ex.submit(design.objective_fd_gradient, tuple(p), d, 211.0, 0.025, Sigma, st) for p in params_list]
+        return [f.result() for f in futs]
+
+
+def _fd_band(out, idx, fds):
+    """The 2 % band with the near-zero rule: |g - g_FD| <= max(0.02 |g_FD|,
+    5 SE_g, 1e-6) for the likelihood-ratio gradient; the sigmoid (pathwise)
+    estimator, biased by O(h^2), within max(0.05 |g_FD|, 20 SE + 2e-3)."""
+    bad, rec = [], []
+    for j, fd in zip(idx, fds):
+        g, se = out["grad_lr"][4 * j:4 * j + 4], out["grad_se"][4 * j:4 * j + 4]
+        gs = out["grad_sig"][4 * j:4 * j + 4]
+        tol = np.maximum(np.maximum(0.02 * np.abs(fd), 5 * se), 1e-6)
+        tol_s = np.maximum(0.05 * np.abs(fd), 20 * se + 2e-3)
+        rec.append({"design": int(j), "grad_lr": g.tolist(), "grad_sig": gs.tolist(), "fd": list(map(float, fd)),
+                    "se": se.tolist()})
+        if not (np.all(np.abs(g - fd) <= tol) and np.all(np.abs(gs - fd) <= tol_s)):
+            bad.append(rec[-1])
+    assert not bad, bad
+    return rec
+
+
+@pytest.fixture(scope="module")
+def c4_full(ctx):
+    prob = workloads.c4()
+    out = run(ctx, prob, seed=0, grad=True, k=4, jac=prob.jac_packed(), h=0.01, graph=True)
+    return prob, out
+
+
+@pytest.fixture(scope="module")
+def c5_full(ctx):
+    prob = workloads.c5()
+    out = run(ctx, prob, seed=0, grad=True, k=4, jac=prob.jac_packed(), h=0.01, graph=True)
+    return prob, out
+
+
+def test_c4_full_gradients_vs_fd(c4_full):
+    prob, out = c4_full
+    idx = sorted(np.random.default_rng(5).choice(prob.n_design, 12, replace=False).tolist())
+    fds = _fd_many([prob.params[j] for j in idx], 10, prob.structures[0])
+    rec = _fd_band(out, idx, fds)
+    report("c4 gradients vs FD of AR(1) quadrature (12 designs x 1e7 draws)", designs=len(idx), per_design=rec)
+
+
+def test_c5_full_gradients_vs_fd(c5_full):
+    prob, out = c5_full
+    idx = workloads.c5_subsample()[:8].tolist()
+    fds = _fd_many([prob.params[j] for j in idx], 20, prob.structures[0])
+    rec = _fd_band(out, idx, fds)
+    report("c5 gradients vs FD of block quadrature (8 designs x 1e7 draws)", designs=len(idx), per_design=rec)
