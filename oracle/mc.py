@@ -36,6 +36,8 @@ def lib():
                                       P(u64), P(u64), P(u64), f64, f64,
                                       P(u64), P(u64), P(f64), P(f64), P(f64)]
         L.oracle_num_threads.restype = ctypes.c_int
+        L.oracle_set_num_threads.argtypes = [ctypes.c_int]
+        L.oracle_set_num_threads.restype = None
         _lib = L
     return _lib
 
@@ -140,9 +142,14 @@ def num_threads():
     return lib().oracle_num_threads()
 
 
+def set_num_threads(n):
+    """Threads of mc_batch's loop over designs from now on (OpenMP)."""
+    lib().oracle_set_num_threads(int(n))
+
+
 def se_binomial(p, n):
     return math.sqrt(max(p * (1.0 - p), 0.0) / n)
 
 
 __all__ = ["philox4x32_10", "philox_stream", "uniform", "normals", "cholesky", "mc_batch",
-           "lr_gradient_mu", "num_threads", "se_binomial", "os"]
+           "lr_gradient_mu", "num_threads", "set_num_threads", "se_binomial", "os"]

@@ -205,6 +205,18 @@ void oracle_mc_batch(int64_t n_design, const int32_t* d, const double* L, const 
     }
 }
 
+/* Threads of the batch loop for the calls that follow (timing on one core
+ * or on all of them); n < 1 is ignored. */
+void oracle_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 int oracle_num_threads(void)
 {
 #ifdef _OPENMP
