@@ -1,16 +1,19 @@
 """Benchmark of the design-objective engine on one GB300 (or N replicas).
 
 Step = one pass of the whole hot path over the d=3 design grid (16 scenarios
-x 64 cutoff quantiles x 64 allocations, 1e6 draws per design): Cholesky of
-each Sigma, the fused sampling kernel (Philox -> Box-Muller -> L z ->
-indicator -> hit counts, with the likelihood-ratio and sigmoid adjoint sums
-in the same pass), the FP64 finalisation (p, SE, gradients w.r.t. cutoff,
+x 64 cutoff quantiles x 64 allocations, 1e6 draws per design, one stream key
+per scenario): Cholesky of each Sigma, the fused shared-draw sampling kernel
+(Philox -> Box-Muller -> L z once per draw and block, then the indicator and
+the likelihood-ratio and sigmoid adjoint sums of every design of the
+scenario against it), the FP64 finalisation (p, SE, gradients w.r.t. cutoff,
 allocation, delta+, delta-) and the local-quadratic smoothing with argmax.
+`per_design_step` times the same step with one stream key per design
+(independent draws), where the per-design kernel makes every draw.
 
 Prints one JSON line.  `value` is draw-evaluations per second over the whole
-job (all ranks); `roofline` refers to the sampling kernel (issue slots of
-its algorithmic operations) and `pipe_bound` to the min-over-pipes bound
-from the instruction-class rates this GPU measures (`mcd_pipe_rate`); `e2e`
+job (all ranks); `roofline` and `pipe_bound` refer to the sampling kernel:
+the min-over-pipes bound from its per-draw-evaluation operation counts and
+the instruction-class rates this GPU measures (`mcd_pipe_rate`); `e2e`
 times the same step through the public API with inputs copied from pinned
 host memory and results copied back; `cpu_baseline` times the FP64 oracle
 on the host and compares its hit counts with the GPU's at the same seed.
@@ -41,11 +44,14 @@ UNIT = "draw-evals/s"
 LANES = 128
 SM_MAX_MHZ = 2070.0
 WORKLOAD = ("d=3 design grid: 16 scenarios x 64 cutoff quantiles x 64 allocation fractions, "
-            "1e6 FP32 draws per design, forward + adjoint (cutoff, allocation, delta+, delta-; "
-            "sigmoid h=1e-2), FP64 finalisation, local-quadratic smoothing + argmax")
+            "1e6 FP32 draws per design (one stream per scenario), forward + adjoint (cutoff, allocation, "
+            "delta+, delta-; sigmoid h=1e-2), FP64 finalisation, local-quadratic smoothing + argmax")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sample_kernel_c2_traffic.txt")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2005_10494_gb300", "csrc", f)
                   for f in ("sample.cuh", "rng.cuh", "mcd_internal.cuh")]
+SHARED_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "shared_kernel_c2_traffic.txt")
+SHARED_SOURCES = [os.path.join(ROOT, "paper_2005_10494_gb300", "csrc", f)
+                  for f in ("shared.cuh", "sample.cuh", "rng.cuh", "mcd_internal.cuh")]
 
 
 # Algorithmic 32-bit operations per draw-evaluation (one design, one draw):
@@ -127,6 +133,75 @@ def class_counts(d, grad):
 MUFU = ("lg2", "sqrt", "sin", "cos", "ex2", "rcp")
 
 
+def shared_class_counts(d, grad, dpt, active=1.0):
+    """Operations per draw-evaluation of the shared-draw kernel (csrc/shared.cuh)
+    for one design and one draw, by instruction class: the draw itself is
+    made once per block for a whole chunk of designs, so its cost vanishes
+    per design.  Forward: d FP32 differences t_i - y_i, their or and sign
+    (d + 1 ALU) and the count add; the draw's row of y is one 16-byte load
+    per 4 coordinates, shared by the thread's dpt designs.  Adjoint: the
+    hit as a 0/1 factor and d FMAs of sum A; d FMAs of the sigmoid
+    exponents, their maximum (d - 1), the range test and the warp vote (ALU),
+    the row of z; and, in the fraction `active` of warp-draws where some
+    lane's draw is within the sigmoid's reach, per coordinate ex2, 1 + e,
+    rcp, the running product, 1 - keep and the FMA of sum G.  The sign test
+    ors the d sign words with three-input logic (ceil((d-1)/2) ops), then a
+    shift and the count add."""
+    rows = -(-d // 4)
+    c = {"mul_wide": 0.0, "alu": (d - 1 + 1) // 2 + 2.0, "ffma": float(d), "lg2": 0.0, "sqrt": 0.0,
+         "sin": 0.0, "cos": 0.0, "ex2": 0.0, "rcp": 0.0, "lds128": rows / float(dpt)}
+    if grad:
+        c["alu"] += 1 + (d - 1) + 3
+        c["ffma"] += 2 * d
+        c["lds128"] += rows / float(dpt)
+        c["ffma"] += active * 4 * d
+        c["ex2"] += active * d
+        c["rcp"] += active * d
+    return c
+
+
+def shared_active_fraction(prob, h, draws=1024, warp=32, seed=0):
+    """Fraction of (32-design block, draw) pairs of the shared-draw kernel in
+    which some design's draw has a sigmoid exponent x_max = max_i (y_i - t_i)
+    log2(e) / h in [-25, 128), i.e. where the kernel evaluates the smoothed
+    indicator (elsewhere it adds exact zeros and skips).  A warp tests 32
+    consecutive designs of a group against one draw; estimated on `draws`
+    normal draws per scenario (numpy FP64, not the kernel's stream: this is
+    a property of the workload)."""
+    rng = np.random.default_rng(seed)
+    tot = act = 0
+    l2e = 1.4426950408889634 / h
+    for s in range(prob.n_scen):
+        idx = np.flatnonzero(prob.design_scen == s)
+        if idx.size == 0:
+            continue
+        L = np.linalg.cholesky(prob.sigmas[s])
+        y = rng.standard_normal((draws, L.shape[0])) @ L.T
+        t = np.stack([prob.t(j) for j in idx])
+        for w0 in range(0, idx.size, warp):
+            xm = ((y[:, None, :] - t[None, w0:w0 + warp, :]) * l2e).max(axis=2)
+            a = ((xm >= -25.0) & (xm < 128.0)).any(axis=1)
+            act += int(a.sum())
+            tot += a.size
+    return act / max(tot, 1)
+
+
+def shared_pipe_bound(rates, d, grad, dpt, active, sm_count, mhz=SM_MAX_MHZ):
+    """The min-over-pipes bound of the shared-draw kernel (as pipe_bound)."""
+    n = shared_class_counts(d, grad, dpt, active)
+    clk = {
+        "alu": n["alu"] / rates["lop3"],
+        "fp32": n["ffma"] / rates["ffma"],
+        "mufu": sum(n[k] / rates[k] for k in MUFU),
+        "lsu": n["lds128"] / rates["lds128"],
+        "issue": sum(n.values()) / LANES,
+    }
+    binding = max(clk, key=clk.get)
+    return {"sm_clk_per_draw": clk, "binding": binding,
+            "bound_draw_evals_per_s": sm_count * mhz * 1e6 / clk[binding], "ops_per_draw": n,
+            "active_fraction": active}
+
+
 def pipe_bound(rates, d, grad, sm_count, mhz=SM_MAX_MHZ):
     """The min-over-pipes bound on draw-evaluations per second: SM clocks per
     draw on each pipe = the draw's operations of that pipe's classes / the
@@ -162,7 +237,8 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the d=10/20, smoothing and C3 lines")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle baseline")
-    ap.add_argument("--case", default=None, choices=["c2-small", "c4-small", "c5-small", "smooth", "c2-shared"],
+    ap.add_argument("--case", default=None, choices=["c2-small", "c4-small", "c5-small", "smooth", "c2-shared",
+                                                      "c2-shared-full"],
                     help="run a small profiling case (a few launches, no timing) and exit")
     return ap.parse_args()
 
@@ -229,6 +305,57 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ CPU oracle
+def host_cpu():
+    """Model name and logical core count of the host (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        fields = dict(line.split(":", 1) for line in out.splitlines() if ":" in line)
+        fields = {k.strip(): v.strip() for k, v in fields.items()}
+        model = fields.get("Model name") or fields.get("Vendor ID")
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"model": model or "unknown", "logical_cores": os.cpu_count()}
+
+
+def quadrature_times():
+    """The deterministic oracle's time per design (FP64, one thread):
+    conditioning with nested Gauss-Legendre on the dense d=3 factor (O1) and
+    the structured forms -- the one-factor integral (equicorrelated d=3),
+    the Markov recursion (AR(1) d=10) and the nested factor integral (block
+    d=20) -- on designs of the d=3, d=10 and d=20 grids."""
+    import workloads
+    from oracle import quad
+    cases = []
+    for k, (q, a) in enumerate([(0.3, 0.4), (0.6, 0.7), (0.85, 0.25), (0.1, 0.55)]):
+        mu, b, _ = workloads.design_at("c2", q, a, scenario=k)
+        rho = workloads.c2_scenarios(16)[k][2]
+        cases.append(("o1_dense_d3", lambda t=b - mu, r=rho: quad.orthant_dense(t, workloads.equicorrelated(3, r))))
+        cases.append(("o2_equi_d3", lambda t=b - mu, r=rho: quad.orthant_equi(t, r)))
+    for q, a in [(0.3, 0.4), (0.7, 0.6)]:
+        mu, b, _ = workloads.design_at("c4", q, a)
+        cases.append(("o2_ar1_d10", lambda t=b - mu: quad.orthant_ar1(t, 0.3)))
+        mu, b, _ = workloads.design_at("c5", q, a)
+        t5 = workloads.tables()["c5"]
+        cases.append(("o2_block_d20", lambda t=b - mu: quad.orthant_block(t, t5["sizes"], t5["rho_in"],
+                                                                          t5["rho_out"])))
+    acc = {}
+    for name, fn in cases:
+        t0 = time.perf_counter()
+        fn()
+        acc.setdefault(name, []).append(time.perf_counter() - t0)
+    return {name + "_ms_per_design": 1000.0 * float(np.mean(v)) for name, v in acc.items()}
+
+
 def cpu_oracle_rate(prob, seconds, h=0.01, seed=0, gpu_hits=None):
     """Time the FP64 oracle (as it stands) on a sample of the workload's designs.
     With gpu_hits (the GPU step's hit counts at the same seed), also report
@@ -248,12 +375,28 @@ def cpu_oracle_rate(prob, seconds, h=0.01, seed=0, gpu_hits=None):
     idx = rng.choice(prob.n_design, n_des, replace=False)
     designs = [{"Sigma": prob.sigmas[prob.design_scen[j]], "t": prob.t(j), "key": int(prob.keys[j]),
                 "n_draws": n} for j in idx]
+    cores = omc.num_threads()
     t0 = time.perf_counter()
     ora = omc.mc_batch(designs, seed, h=h, grad=True)
     dt = time.perf_counter() - t0
-    rec = {"value": n_des * n / dt, "unit": UNIT, "cores": omc.num_threads(), "kind": "oracle",
+    rec = {"value": n_des * n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
            "sample": "%d random designs of the d=3 grid x %d draws each (their full draw count), "
                      "FP64 estimator with adjoint sums, %.1f s" % (n_des, n, dt)}
+    # one thread on a quarter of the time budget: the per-core figure beside
+    # the all-core one, and the host it ran on
+    n1 = int(max(1, min(n_des, round(seconds / 4.0 / (per_draw * cores) / n))))
+    omc.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        omc.mc_batch(designs[:n1], seed, h=h, grad=True)
+        dt1 = time.perf_counter() - t0
+    finally:
+        omc.set_num_threads(cores)
+    rec["single_thread"] = {"value": n1 * n / dt1, "unit": UNIT, "cores": 1,
+                            "sample": "%d of the designs above, %.1f s" % (n1, dt1)}
+    rec["per_core_all_cores"] = rec["value"] / cores
+    rec["host"] = host_cpu()
+    rec["quadrature"] = quadrature_times()
     if gpu_hits is not None:
         g = np.asarray(gpu_hits, dtype=np.int64)[idx]
         o = np.asarray(ora["hits"], dtype=np.int64)
@@ -323,29 +466,49 @@ def max_over_ranks(t, device):
 
 
 # ------------------------------------------------------------ our arm
-def traffic_record(tiles):
-    """DRAM bytes of one sampling launch of `tiles` tiles, from the committed
-    ncu capture of a small case (traffic grows with the tile count), or None
-    when the kernel sources changed since that capture."""
-    if not os.path.exists(TRAFFIC_FILE):
+def read_record(path, sources):
+    """The key: value lines of a committed ncu summary, or None when it is
+    missing or the kernel sources no longer hash to its src_sha256."""
+    if not os.path.exists(path):
         return None
     rec = {}
-    with open(TRAFFIC_FILE) as f:
+    with open(path) as f:
         for ln in f:
             if ":" in ln and not ln.startswith("#"):
                 k, v = ln.split(":", 1)
                 rec[k.strip()] = v.strip()
     h = hashlib.sha256()
-    for p in KERNEL_SOURCES:
+    for p in sources:
         with open(p, "rb") as f:
             h.update(f.read())
-    if rec.get("src_sha256") != h.hexdigest():
+    return rec if rec.get("src_sha256") == h.hexdigest() else None
+
+
+def traffic_record(tiles):
+    """DRAM bytes of one per-design sampling launch of `tiles` tiles, from the
+    committed ncu capture of a small case (traffic grows with the tile
+    count), or None when the kernel sources changed since that capture."""
+    rec = read_record(TRAFFIC_FILE, KERNEL_SOURCES)
+    if rec is None:
         return None
     try:
         per_tile = (float(rec["dram_bytes_read_small"]) + float(rec["dram_bytes_write_small"])) / float(rec["tiles_small"])
     except (KeyError, ValueError, ZeroDivisionError):
         return None
     return per_tile * tiles
+
+
+def shared_traffic_record():
+    """DRAM bytes of one launch of the shared-draw adjoint kernel on the full
+    d=3 grid step, from the committed ncu capture of that launch, or None when
+    the kernel sources changed since."""
+    rec = read_record(SHARED_TRAFFIC_FILE, SHARED_SOURCES)
+    if rec is None:
+        return None
+    try:
+        return float(rec["dram_bytes_read"]) + float(rec["dram_bytes_write"])
+    except (KeyError, ValueError):
+        return None
 
 
 def kernel_rate(pkg, ctx, prob, grad, reps=2, h=0.01):
@@ -368,6 +531,82 @@ def kernel_rate(pkg, ctx, prob, grad, reps=2, h=0.01):
     return prob.total_draws() / (best / 1e3), best
 
 
+def shared_dpt(d, grad):
+    """Designs per thread of the shared-draw kernel (SharedShape in shared.cuh)."""
+    if grad:
+        return 4 if d <= 4 else (2 if d <= 8 else 1)
+    return 4 if d <= 10 else 2
+
+
+def timed_steps(step, steps, stream, flush, kernel_ms):
+    """Run `steps` steps bracketed by CUDA events on `stream`, flushing L2
+    before each; returns (per-step ms, per-step sampling-kernel ms, wall s)."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    kms = []
+    wall0 = time.perf_counter()
+    for s in range(steps):
+        flush.fill_(float(s))                 # evict L2 between steps (256 MB > 126 MB L2)
+        ev[s][0].record(stream)
+        step(s)
+        ev[s][1].record(stream)
+        kms.append(kernel_ms())               # waits for this step
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev], kms, time.perf_counter() - wall0
+
+
+def per_design_step(pkg, ctx, args, rates, sm_count, stream, flush):
+    """The same step with independent stream keys (one per design): the
+    per-design kernel (Philox -> Box-Muller -> L z -> indicator -> sums per
+    draw and design), timed like the headline step, with its roofline."""
+    import torch
+
+    import workloads
+    prob = workloads.c2(keys="independent")
+    dp = pkg.DeviceProblem.from_workload(prob)
+    jac = torch.as_tensor(prob.jac_packed(), dtype=torch.float64, device="cuda")
+    plan = pkg.Plan(ctx, dp, grad=True, k=4, autotune=True, graph=True, timing=True)
+    S, G1, G2 = prob.n_scen, prob.grid[0], prob.grid[1]
+
+    def step(seed):
+        out = plan.grad(seed, jac, 0.01, stream=stream)
+        pkg.mc_smooth_argmax(ctx, out["p"], S, G1, G2, bandwidth=3.0, degree=2, stream=stream)
+
+    for w in range(args.warmup):
+        step(2000 + w)
+    torch.cuda.synchronize()
+    step_ms, kms, _ = timed_steps(step, args.steps, stream, flush, plan.kernel_ms)
+    ctx.sync_status()
+    draws = prob.total_draws()
+    kernel_ms = statistics.mean(kms)
+    ops = ops_per_draw(3, True)
+    peak_ops = sm_count * LANES * SM_MAX_MHZ * 1e6
+    achieved = ops * draws / (kernel_ms / 1e3)
+    pb = pipe_bound(rates, 3, True, sm_count)
+    rate = draws / (kernel_ms / 1e3)
+    fp32 = fp32_flops_per_draw(3, True) * rate
+    fp32_peak = sm_count * LANES * 2 * SM_MAX_MHZ * 1e6
+    cfg3 = plan.config(3)
+    res = {"workload": "the headline step with one stream key per design (independent draws): "
+                       "per-design sampling kernel",
+           "value": args.steps * draws / (sum(step_ms) / 1e3), "unit": UNIT, "ms_per_step": statistics.mean(step_ms),
+           "launch": {"threads": cfg3["threads"], "tile_draws": cfg3["tile_draws"],
+                      "blocks_per_sm": cfg3["blocks_per_sm"], "tiles": plan.tiles()},
+           "roofline": {"bound": "issue", "achieved": achieved / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
+                        "frac": achieved / peak_ops, "traffic": traffic_record(plan.tiles()),
+                        "kernel": "sample_kernel<3,3,grad,float>", "kernel_ms": kernel_ms, "ops_per_draw": ops,
+                        "peak_basis": "%d SMs x 128 issue slots x %.0f MHz (max SM clock): one warp "
+                                      "instruction per scheduler per clock" % (sm_count, SM_MAX_MHZ)},
+           "pipe_bound": {"kernel": "sample_kernel<3,3,grad,float>", "achieved": rate,
+                          "bound": pb["bound_draw_evals_per_s"], "unit": UNIT,
+                          "frac": rate / pb["bound_draw_evals_per_s"], "binding": pb["binding"],
+                          "sm_clk_per_draw": pb["sm_clk_per_draw"], "ops_per_draw": pb["ops_per_draw"]},
+           "fp32_pipe": {"achieved_tflops": fp32 / 1e12, "peak_tflops": fp32_peak / 1e12, "frac": fp32 / fp32_peak,
+                         "flops_per_draw": fp32_flops_per_draw(3, True)}}
+    plan.close()
+    return res
+
+
 def run_ours(args, rank, world):
     import torch
 
@@ -377,12 +616,15 @@ def run_ours(args, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     ctx = pkg.Context(dev.index)
+    # the d=3 grid with one stream key per scenario: the 4096 designs of a
+    # scenario share their draws (common random numbers), so the plan takes
+    # the shared-draw kernel; hit counts are those of the per-design kernel
     prob = workloads.c2()
     if world > 1:
         prob.keys = rank_keys(prob.keys, rank)
     dp = pkg.DeviceProblem.from_workload(prob)
     jac = torch.as_tensor(prob.jac_packed(), dtype=torch.float64, device=dev)
-    plan = pkg.Plan(ctx, dp, grad=True, k=4, autotune=True, graph=True, timing=True)
+    plan = pkg.Plan(ctx, dp, grad=True, k=4, graph=True, timing=True, shared=True)
     S, G1, G2 = prob.n_scen, prob.grid[0], prob.grid[1]
     stream = torch.cuda.Stream(device=dev)      # capturable stream for the plan's CUDA graph
     stream.wait_stream(torch.cuda.current_stream())
@@ -406,18 +648,7 @@ def run_ours(args, rank, world):
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    kms = []
-    wall0 = time.perf_counter()
-    for s in range(args.steps):
-        flush.fill_(float(s))                 # evict L2 between steps (256 MB > 126 MB L2)
-        ev[s][0].record(stream)
-        step(s)
-        ev[s][1].record(stream)
-        kms.append(plan.kernel_ms())          # waits for this step
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - wall0
-    step_ms = [a.elapsed_time(b) for a, b in ev]
+    step_ms, kms, wall = timed_steps(step, args.steps, stream, flush, plan.kernel_ms)
     t_total = sum(step_ms) / 1e3
     t_total = max_over_ranks(t_total, dev)
     clk = clocks.stop() if rank == 0 else None
@@ -429,13 +660,20 @@ def run_ours(args, rank, world):
     if rank != 0:
         return
 
-    cfg3 = plan.config(3)
-    ops = ops_per_draw(3, True)
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak_ops = sm_count * LANES * SM_MAX_MHZ * 1e6
-    achieved = ops * draws / (kernel_ms / 1e3)
-    traffic = traffic_record(plan.tiles())
-    fp32 = fp32_flops_per_draw(3, True) * draws / (kernel_ms / 1e3)
+    rate = draws / (kernel_ms / 1e3)
+    # instruction-class rates of this GPU (own microbenchmarks), for the
+    # min-over-pipes bounds
+    rates = pkg.pipe_rates(ctx, iters=4096, stream=stream)
+    active = shared_active_fraction(prob, 0.01, draws=512)
+    dpt = shared_dpt(3, True)
+    spb = shared_pipe_bound(rates, 3, True, dpt, active, sm_count)
+    n = spb["ops_per_draw"]
+    # FP32 flops per draw-evaluation (FMA = 2): the d differences, the sum A
+    # and the sigmoid exponents (5d); where the sigmoid is evaluated, 1 + e,
+    # the running product, 1 - keep and the sum G (5d)
+    fp32_flops = 5 * 3 * (1.0 + active)
+    fp32 = fp32_flops * rate
     fp32_peak = sm_count * LANES * 2 * SM_MAX_MHZ * 1e6
 
     # e2e: same step through the public API from pinned host buffers
@@ -471,19 +709,22 @@ def run_ours(args, rank, world):
         e2e_times.append(time.perf_counter() - t0)
     e2e_value = world * draws * args.steps / sum(e2e_times)
 
-    # instruction-class rates of this GPU (own microbenchmarks), for the
-    # min-over-pipes bound
-    rates = pkg.pipe_rates(ctx, iters=4096, stream=stream)
-    pb = pipe_bound(rates, 3, True, sm_count)
-    achieved_draws = draws / (kernel_ms / 1e3)
+    out0, _ = step(0)                       # the first timed step's seed, for the oracle comparison
+    hits0 = out0["hits"].cpu().numpy()
+    ctx.sync_status()
+
+    per = per_design_step(pkg, ctx, args, rates, sm_count, stream, flush)
+    # the per-design kernel on the same (common-random-number) keys gives
+    # the same hit counts
+    ref_plan = pkg.Plan(ctx, dp, graph=False)
+    same_hits = bool(np.array_equal(ref_plan.eval(0, stream=stream)["hits"].cpu().numpy(), hits0))
+    ref_plan.close()
+    ctx.sync_status()
 
     extras = {}
     if not args.no_extras:
         extras = run_extras(pkg, ctx, prob, rates, sm_count)
 
-    out0, _ = step(0)                       # the first timed step's seed, for the oracle comparison
-    hits0 = out0["hits"].cpu().numpy()
-    ctx.sync_status()
     cpu = cpu_oracle_rate(prob, args.cpu_seconds, gpu_hits=hits0)
 
     line = {
@@ -492,24 +733,24 @@ def run_ours(args, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "designs": int(J), "draws_per_design": int(prob.n_draws[0]),
                    "d": 3, "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "stream_keys": "one per scenario (common random numbers): shared-draw kernel",
                    "l2": "flushed between steps (256 MB write); inputs and outputs are < 20 MB",
-                   "launch": {"threads": cfg3["threads"], "tile_draws": cfg3["tile_draws"],
-                              "blocks_per_sm": cfg3["blocks_per_sm"], "tiles": plan.tiles(),
-                              "cuda_graph": True, "autotuned": True}},
-        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
-                     "frac": achieved / peak_ops, "traffic": traffic,
-                     "kernel": "sample_kernel<3,3,grad,float>", "kernel_ms": kernel_ms,
-                     "ops_per_draw": ops, "peak_basis": "%d SMs x 128 lanes x %.0f MHz (max SM clock), "
-                     "one 32-bit op per lane per clock" % (sm_count, SM_MAX_MHZ)},
-        "pipe_bound": {"kernel": "sample_kernel<3,3,grad,float>", "achieved": achieved_draws,
-                       "bound": pb["bound_draw_evals_per_s"], "unit": UNIT,
-                       "frac": achieved_draws / pb["bound_draw_evals_per_s"], "binding": pb["binding"],
-                       "sm_clk_per_draw": pb["sm_clk_per_draw"], "ops_per_draw": pb["ops_per_draw"],
-                       "rates_ops_per_sm_clk": rates,
-                       "basis": "draw-evaluations per second if the busiest pipe ran at the rate the "
-                                "microbenchmarks measured, at %.0f MHz" % SM_MAX_MHZ},
+                   "launch": {"kernel": "shared_kernel<3,grad>", "designs_per_thread": dpt, "cuda_graph": True}},
+        "roofline": {"bound": spb["binding"], "achieved": rate, "peak": spb["bound_draw_evals_per_s"],
+                     "unit": UNIT, "frac": rate / spb["bound_draw_evals_per_s"],
+                     "traffic": shared_traffic_record(), "kernel": "shared_kernel<3,grad>", "kernel_ms": kernel_ms,
+                     "peak_basis": "min over pipes (issue 128 per SM clock; ALU, FP32, MUFU and shared-load "
+                                   "rates measured by mcd_pipe_rate) of the per-draw-evaluation operation counts, "
+                                   "%d SMs x %.0f MHz; the sigmoid's exponentials in the measured fraction "
+                                   "%.3f of warp-draws that reach it" % (sm_count, SM_MAX_MHZ, active)},
+        "pipe_bound": {"kernel": "shared_kernel<3,grad>", "achieved": rate, "bound": spb["bound_draw_evals_per_s"],
+                       "unit": UNIT, "frac": rate / spb["bound_draw_evals_per_s"], "binding": spb["binding"],
+                       "sm_clk_per_draw": spb["sm_clk_per_draw"], "ops_per_draw": n,
+                       "active_fraction": active, "rates_ops_per_sm_clk": rates},
         "fp32_pipe": {"achieved_tflops": fp32 / 1e12, "peak_tflops": fp32_peak / 1e12, "frac": fp32 / fp32_peak,
-                      "flops_per_draw": fp32_flops_per_draw(3, True)},
+                      "flops_per_draw": fp32_flops},
+        "hits_equal_per_design_kernel": same_hits,
+        "per_design_step": per,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         # per step: Cholesky, sampling, finalisation, smoothing weights,
         # stencil and argmax
@@ -776,8 +1017,12 @@ def paper_optimisation(pkg, ctx):
 
 def dim_line(rf, rg, d, rates, sm_count):
     bf, bg = pipe_bound(rates, d, False, sm_count), pipe_bound(rates, d, True, sm_count)
+    fp32_peak = sm_count * LANES * 2 * SM_MAX_MHZ * 1e6
     return {"fwd": rf, "adj": rg, "adjoint_overhead": rf / rg,
             "fwd_op_frac": rf * ops_per_draw(d, False) / (sm_count * LANES * SM_MAX_MHZ * 1e6),
+            "adj_op_frac": rg * ops_per_draw(d, True) / (sm_count * LANES * SM_MAX_MHZ * 1e6),
+            "fwd_fp32_pipe_frac": rf * fp32_flops_per_draw(d, False) / fp32_peak,
+            "adj_fp32_pipe_frac": rg * fp32_flops_per_draw(d, True) / fp32_peak,
             "fwd_pipe_bound": {"binding": bf["binding"], "bound": bf["bound_draw_evals_per_s"],
                                "frac": rf / bf["bound_draw_evals_per_s"]},
             "adj_pipe_bound": {"binding": bg["binding"], "bound": bg["bound_draw_evals_per_s"],
@@ -851,9 +1096,10 @@ def run_case(case):
             pkg.mc_smooth_argmax(ctx, v, S, G, G, bandwidth=3.0, degree=2)
         ctx.sync_status()
         return
-    if case == "c2-shared":
-        # two scenarios of the d=3 grid (2 x 4096 designs, one stream each), 1e6 draws
-        prob = workloads.c2(n_scen=2, n_draws=1_000_000)
+    if case in ("c2-shared", "c2-shared-full"):
+        # two scenarios of the d=3 grid (2 x 4096 designs, one stream each),
+        # or the whole grid of the timed step, 1e6 draws
+        prob = workloads.c2(n_scen=2 if case == "c2-shared" else 16, n_draws=1_000_000)
         dp = pkg.DeviceProblem.from_workload(prob)
         jac = torch.as_tensor(prob.jac_packed(), dtype=torch.float64, device="cuda")
         fwd = pkg.Plan(ctx, dp, shared=True)

@@ -115,7 +115,7 @@ mcd_status mcd_sync_status(mcd_ctx* ctx, mcd_stream stream);
  * MCD_SHARED_MIN such designs are evaluated by the shared-draw kernel, which
  * makes each draw once per block and tests it against every design of the
  * group: hit counts are bit-identical to the per-design kernel, gradient
- * sums equal up to the order of FP32 additions.  Smaller groups keep the
+ * sums equal up to FP32 rounding.  Smaller groups keep the
  * per-design kernel.  Not with MCD_PLAN_FP64 (MCD_EUNSUPPORTED). */
 #define MCD_SHARED_MIN    32
 
@@ -124,7 +124,11 @@ mcd_status mcd_sync_status(mcd_ctx* ctx, mcd_stream stream);
  * the tile schedule and allocates the workspace (blocking).  With
  * MCD_PLAN_AUTOTUNE it runs timing launches on the GPU (blocking).
  * k: number of design parameters of the Jacobian that mcd_plan_grad takes
- * (1..8), or 0 for gradients with respect to mu. */
+ * (1..8), or 0 for gradients with respect to mu.
+ * With MCD_PLAN_GRAD a design's draws are spread over at most 32 batch
+ * slots whose sums are 64-bit fixed point; a design that would put more
+ * than 2^32 draws into one slot (about 1.3e11 draws per design) is refused
+ * with MCD_EINVAL and its index, since its sums could overflow. */
 mcd_status mcd_plan_create(mcd_ctx* ctx, const mcd_problem* prob, int32_t flags,
                            int32_t k, mcd_plan** plan);
 /* Free a plan.  It may be called before or after mcd_destroy of its context
@@ -178,6 +182,19 @@ mcd_status mcd_plan_kernel_ms(mcd_plan* plan, float* ms);
 mcd_status mc_design_eval(mcd_ctx* ctx, const mcd_problem* prob, uint64_t seed,
                           uint64_t* hits, double* p, double* se, mcd_stream stream);
 
+/* Estimate p and its derivatives for every design in one call (plan with
+ * MCD_PLAN_GRAD and k, launch mcd_plan_grad, release).  Appendix A.3 shows
+ * that the objective is a smooth function of the design, and its derivative
+ * an integral over the same law as p itself, so it is estimated from the
+ * same draws:
+ *   likelihood ratio: grad_mu p = Sigma^-1 E[(1_R - p)(X - mu)]
+ *     = L^-T E[(1_R - p) z] (X = mu + L z; the control variate p E[z] = 0
+ *     lowers the variance), chained as grad_theta p = -(dt/dtheta)^T grad_mu p;
+ *   sigmoid (pathwise): the derivative of E[1 - prod_i sigma((b_i - X_i)/h)],
+ *     a smoothed indicator with bandwidth h, when h_sigmoid > 0.
+ * Arguments and outputs as in mcd_plan_create (k) and mcd_plan_grad; the
+ * workspace is allocated and freed in stream order (cudaMallocAsync /
+ * cudaFreeAsync), so not for use under stream capture. */
 mcd_status mc_design_grad(mcd_ctx* ctx, const mcd_problem* prob, uint64_t seed,
                           int32_t k, const double* dt_dtheta, double h_sigmoid,
                           uint64_t* hits, double* p, double* grad_lr, double* grad_sig,
@@ -310,6 +327,17 @@ mcd_status mc_smooth_argmax(mcd_ctx* ctx, int32_t n_scen, int32_t g1, int32_t g2
                             double* smoothed, int64_t* argmax_idx, double* argmax_val,
                             int64_t* raw_idx, double* raw_val, mcd_stream stream);
 
+/* mc_smooth_argmax on FP32 grids (the same smoothing of Sec. 2.3, weights,
+ * edge rules, limits and errors): value, smoothed, argmax_val and raw_val are
+ * FP32 (DEVICE).  The stencil already runs in FP32, so the results equal
+ * mc_smooth_argmax's on the same values rounded to FP32; the grid moves half
+ * the bytes through HBM.  Estimates p in [0, 1] lose nothing that matters
+ * against their Monte Carlo error (FP32 spacing 6e-8 at 1). */
+mcd_status mc_smooth_argmax_f32(mcd_ctx* ctx, int32_t n_scen, int32_t g1, int32_t g2,
+                                const float* value, double bandwidth, int32_t degree,
+                                float* smoothed, int64_t* argmax_idx, float* argmax_val,
+                                int64_t* raw_idx, float* raw_val, mcd_stream stream);
+
 /* ---- unit-check entry points -------------------------------------------- */
 
 /* Normals m_begin .. m_begin+count-1 of stream (seed, key) exactly as the
@@ -343,12 +371,14 @@ mcd_status mcd_debug_fail_next(mcd_ctx* ctx, int32_t cuda_error);
 #define MCD_PIPE_MIXED    10   /* half fma.rn.f32, half lop3.b32 (co-issue)        */
 #define MCD_PIPE_LDS128   11   /* ld.shared.v4 at a warp-uniform address (L, d > 6) */
 #define MCD_PIPE_PHILOX   12   /* Philox rounds 2..10 as sampled, per wide multiply */
-#define MCD_PIPE_COUNT    13
+#define MCD_PIPE_FFMA2    13   /* fma.rn.f32x2: two FP32 FMAs per instruction (L z) */
+#define MCD_PIPE_COUNT    14
 
 /* Throughput of one instruction class on this device, in operations per SM
  * clock: the median over SMs of a microbenchmark in which every thread runs
  * eight dependency chains of that instruction, 8 blocks of 256 threads per
- * SM, timed with the SM's cycle counter.  With the per-draw operation counts
+ * SM, timed with the SM's cycle counter (MCD_PIPE_FFMA2: packed instructions,
+ * each two FMAs, per SM clock).  With the per-draw operation counts
  * of the estimator (Sec. 2.2) this bounds draw-evaluations per clock per SM
  * from above.
  *   op: MCD_PIPE_*;  iters: chain steps per thread, 1 <= iters <= 2^20 (each

@@ -19,7 +19,8 @@ MCD_ANY_EXCEEDS, MCD_ALL_BELOW = 0, 1
 MCD_PLAN_GRAD, MCD_PLAN_AUTOTUNE, MCD_PLAN_GRAPH, MCD_PLAN_FP64, MCD_PLAN_TIMING, MCD_PLAN_SHARED = 1, 2, 4, 8, 16, 32
 MCD_SHARED_MIN = 32
 # instruction classes of mcd_pipe_rate, in MCD_PIPE_* order
-PIPE_CLASSES = ("mul_wide", "mad_lo", "lop3", "ffma", "lg2", "sqrt", "sin", "cos", "ex2", "rcp", "mixed", "lds128", "philox")
+PIPE_CLASSES = ("mul_wide", "mad_lo", "lop3", "ffma", "lg2", "sqrt", "sin", "cos", "ex2", "rcp", "mixed", "lds128", "philox",
+                "ffma2")
 MCD_MAX_D = 20
 
 _c_i32p = ctypes.POINTER(ctypes.c_int32)
@@ -69,6 +70,7 @@ def load(path=LIB_PATH):
         "mc_design_eval": (i32, [vp, ctypes.POINTER(CProblem), u64, vp, vp, vp, vp]),
         "mc_design_grad": (i32, [vp, ctypes.POINTER(CProblem), u64, i32, vp, f64, vp, vp, vp, vp, vp, vp]),
         "mc_smooth_argmax": (i32, [vp, i32, i32, i32, vp, f64, i32, vp, vp, vp, vp, vp, vp]),
+        "mc_smooth_argmax_f32": (i32, [vp, i32, i32, i32, vp, f64, i32, vp, vp, vp, vp, vp, vp]),
         "mc_fwer_calibrate": (i32, [vp, ctypes.POINTER(CProblem), vp, f64, i32, u64, vp, vp, vp, vp]),
         "mc_tps_fit": (i32, [vp, i32, i32, i32, vp, vp, f64, vp, vp, vp]),
         "mc_tps_argmax": (i32, [vp, i32, i32, i32, vp, vp, vp, vp, vp, i32, vp, vp, vp]),
@@ -373,17 +375,24 @@ def mc_tps_argmax(ctx, x, fit, lo, hi, iters=200, stream=None):
 
 def mc_smooth_argmax(ctx, values, n_scen, g1, g2, bandwidth=3.0, degree=2, stream=None, smoothed=True,
                      raw=False):
-    """Smooth n_scen grids of g1 x g2 values (FP64 CUDA tensor) and take
+    """Smooth n_scen grids of g1 x g2 values (an FP64 CUDA tensor:
+    mc_smooth_argmax; FP32: mc_smooth_argmax_f32, outputs FP32) and take
     argmaxes; raw=True also returns the argmax of the unsmoothed values."""
     torch = _torch()
     dev = values.device
-    sm = torch.empty(n_scen * g1 * g2, dtype=torch.float64, device=dev) if smoothed else None
+    if values.dtype == torch.float32:
+        fn, ft = ctx.lib.mc_smooth_argmax_f32, torch.float32
+    elif values.dtype == torch.float64:
+        fn, ft = ctx.lib.mc_smooth_argmax, torch.float64
+    else:
+        raise TypeError("values must be float64 or float32")
+    sm = torch.empty(n_scen * g1 * g2, dtype=ft, device=dev) if smoothed else None
     idx = torch.empty(n_scen, dtype=torch.int64, device=dev)
-    val = torch.empty(n_scen, dtype=torch.float64, device=dev)
+    val = torch.empty(n_scen, dtype=ft, device=dev)
     ridx = torch.empty(n_scen, dtype=torch.int64, device=dev) if raw else None
-    rval = torch.empty(n_scen, dtype=torch.float64, device=dev) if raw else None
-    ctx.check(ctx.lib.mc_smooth_argmax(ctx.handle, n_scen, g1, g2, _ptr(values), float(bandwidth), degree,
-                                       _ptr(sm), _ptr(idx), _ptr(val), _ptr(ridx), _ptr(rval), _stream(stream)))
+    rval = torch.empty(n_scen, dtype=ft, device=dev) if raw else None
+    ctx.check(fn(ctx.handle, n_scen, g1, g2, _ptr(values), float(bandwidth), degree,
+                 _ptr(sm), _ptr(idx), _ptr(val), _ptr(ridx), _ptr(rval), _stream(stream)))
     return {"smoothed": sm, "argmax_idx": idx, "argmax_val": val, "raw_idx": ridx, "raw_val": rval}
 
 

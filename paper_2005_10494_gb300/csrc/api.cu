@@ -396,6 +396,25 @@ mcd_status plan_build(mcd_ctx* ctx, const mcd_problem* pr, int32_t flags, int32_
     pl->n_tiles = total_tiles;
     pl->batches = static_cast<int>(std::min<int64_t>(kMaxBatches, max_tiles));
     const int B = pl->batches;
+    // A gradient slot is a signed 64-bit fixed-point sum at 2^-28 of |z| <=
+    // sqrt(48 ln 2) < 5.8 per draw; at most 2^32 draws per slot keep it
+    // below 5.8 * 2^60 < 2^63.
+    constexpr uint64_t kMaxSlotDraws = 1ull << 32;
+    if (grad_kernel) {
+        for (int j = 0; j < J; ++j) {
+            const int64_t T = pl->tile_draws_of_d[designs[j].d];
+            const uint64_t per = static_cast<uint64_t>((tiles_of[j] + B - 1) / B) * static_cast<uint64_t>(T);
+            if (per > kMaxSlotDraws)
+                return fail(ctx, MCD_EINVAL, "n_draws too large for a gradient plan (2^32 draws per batch slot, 32 slots)", j);
+        }
+        for (const SChunk& c : chunks) {
+            const int j0 = groups[c.g][0];
+            const int64_t T = stile_draws[scen_d[pr->design_scen[j0]]];
+            const uint64_t ranges = (n_draws[j0] + T - 1) / T;
+            if ((ranges + B - 1) / B * static_cast<uint64_t>(T) > kMaxSlotDraws)
+                return fail(ctx, MCD_EINVAL, "n_draws too large for a gradient plan (2^32 draws per batch slot, 32 slots)", j0);
+        }
+    }
     for (int j = 0; j < J; ++j) designs[j].acc_off = 3 * designs[j].vec_off * B;
     pl->gacc_len = static_cast<size_t>(3) * vo * B;
 
@@ -1132,10 +1151,15 @@ mcd_status mc_tps_argmax(mcd_ctx* ctx, int32_t n_surf, int32_t n_pts, int32_t k,
     return MCD_OK;
 }
 
-mcd_status mc_smooth_argmax(mcd_ctx* ctx, int32_t n_scen, int32_t g1, int32_t g2, const double* value,
-                            double bandwidth, int32_t degree, double* smoothed, int64_t* argmax_idx,
-                            double* argmax_val, int64_t* raw_idx, double* raw_val, mcd_stream stream) {
-    NvtxRange nvtx_("mc_smooth_argmax");
+}  // extern "C"
+
+namespace {
+
+template <typename T>
+mcd_status smooth_call(const char* name, mcd_ctx* ctx, int32_t n_scen, int32_t g1, int32_t g2, const T* value,
+                       double bandwidth, int32_t degree, T* smoothed, int64_t* argmax_idx, T* argmax_val,
+                       int64_t* raw_idx, T* raw_val, mcd_stream stream) {
+    NvtxRange nvtx_(name);
     if (!ctx) return MCD_EINVAL;
     if (n_scen < 1 || g1 < 1 || g2 < 1) return fail(ctx, MCD_EINVAL, "n_scen, g1, g2 must be >= 1");
     if (static_cast<int64_t>(g1) * g2 >= (1ll << 31)) return fail(ctx, MCD_EINVAL, "grid too large");
@@ -1158,11 +1182,34 @@ mcd_status mc_smooth_argmax(mcd_ctx* ctx, int32_t n_scen, int32_t g1, int32_t g2
     float* w32 = reinterpret_cast<float*>(w64 + nw);
     double* pv = reinterpret_cast<double*>(reinterpret_cast<char*>(w32) + ((nw * sizeof(float) + 15) / 16) * 16);
     int64_t* pi = reinterpret_cast<int64_t*>(pv + nc);
-    cudaError_t e = smooth_argmax(n_scen, g1, g2, value, bandwidth, degree, smoothed, argmax_idx, argmax_val,
-                                  raw_idx, raw_val, w64, w32, pv, pi, ctx->d_status, s);
+    cudaError_t e;
+    if constexpr (sizeof(T) == 8)
+        e = smooth_argmax(n_scen, g1, g2, value, bandwidth, degree, smoothed, argmax_idx, argmax_val, raw_idx, raw_val,
+                          w64, w32, pv, pi, ctx->d_status, s);
+    else
+        e = smooth_argmax_f32(n_scen, g1, g2, value, bandwidth, degree, smoothed, argmax_idx, argmax_val, raw_idx,
+                              raw_val, w64, w32, pv, pi, ctx->d_status, s);
     cudaFreeAsync(ws, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "smoothing launch");
     return MCD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mcd_status mc_smooth_argmax(mcd_ctx* ctx, int32_t n_scen, int32_t g1, int32_t g2, const double* value,
+                            double bandwidth, int32_t degree, double* smoothed, int64_t* argmax_idx,
+                            double* argmax_val, int64_t* raw_idx, double* raw_val, mcd_stream stream) {
+    return smooth_call<double>("mc_smooth_argmax", ctx, n_scen, g1, g2, value, bandwidth, degree, smoothed,
+                               argmax_idx, argmax_val, raw_idx, raw_val, stream);
+}
+
+mcd_status mc_smooth_argmax_f32(mcd_ctx* ctx, int32_t n_scen, int32_t g1, int32_t g2, const float* value,
+                                double bandwidth, int32_t degree, float* smoothed, int64_t* argmax_idx,
+                                float* argmax_val, int64_t* raw_idx, float* raw_val, mcd_stream stream) {
+    return smooth_call<float>("mc_smooth_argmax_f32", ctx, n_scen, g1, g2, value, bandwidth, degree, smoothed,
+                              argmax_idx, argmax_val, raw_idx, raw_val, stream);
 }
 
 mcd_status mcd_debug_normals(mcd_ctx* ctx, uint64_t seed, uint64_t key, uint64_t m_begin, uint64_t count, float* z32,

@@ -41,8 +41,11 @@ struct NoAllocScratch {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
 
-// Device address of the scratch array, looked up once per device.
+// Per device, looked up once: the device address of the scratch array, the
+// SM count and the resident blocks per SM of each dimension's kernel.
 NoAllocScratch* g_scratch_ptr[64] = {};
+int g_sm_count[64] = {};
+int g_blocks_per_sm[64][kMaxD + 1] = {};
 std::mutex g_scratch_mu;
 
 // Sigma = L L^T for the one scenario (FP64, lower triangle read), FP32 copy.
@@ -129,10 +132,19 @@ __global__ void noalloc_finalize_kernel(const NoAllocScratch* sc, int32_t n_desi
 
 template <int D>
 cudaError_t launch_noalloc_sample(const SampleParams& P, NoAllocScratch* sc, int32_t J, uint64_t N, int64_t T,
-                                  int64_t tpd, int sms, cudaStream_t stream) {
-    int bps = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, noalloc_sample_kernel<D>, 256, 0);
-    if (e != cudaSuccess) return e;
+                                  int64_t tpd, int sms, int device, cudaStream_t stream) {
+    int bps;
+    {
+        std::lock_guard<std::mutex> lk(g_scratch_mu);
+        bps = g_blocks_per_sm[device][D];
+    }
+    if (bps == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, noalloc_sample_kernel<D>, 256, 0);
+        if (e != cudaSuccess) return e;
+        bps = std::max(bps, 1);
+        std::lock_guard<std::mutex> lk(g_scratch_mu);
+        g_blocks_per_sm[device][D] = bps;
+    }
     const int64_t n_tiles = static_cast<int64_t>(J) * tpd;
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(n_tiles, static_cast<int64_t>(std::max(bps, 1)) * sms));
     noalloc_sample_kernel<D><<<static_cast<unsigned>(grid), 256, 0, stream>>>(P, sc, J, N, T, tpd);
@@ -141,9 +153,9 @@ cudaError_t launch_noalloc_sample(const SampleParams& P, NoAllocScratch* sc, int
 
 template <int D>
 cudaError_t dispatch_noalloc(int d, const SampleParams& P, NoAllocScratch* sc, int32_t J, uint64_t N, int64_t T,
-                             int64_t tpd, int sms, cudaStream_t stream) {
-    if (d == D) return launch_noalloc_sample<D>(P, sc, J, N, T, tpd, sms, stream);
-    if constexpr (D < kMaxD) return dispatch_noalloc<D + 1>(d, P, sc, J, N, T, tpd, sms, stream);
+                             int64_t tpd, int sms, int device, cudaStream_t stream) {
+    if (d == D) return launch_noalloc_sample<D>(P, sc, J, N, T, tpd, sms, device, stream);
+    if constexpr (D < kMaxD) return dispatch_noalloc<D + 1>(d, P, sc, J, N, T, tpd, sms, device, stream);
     return cudaErrorInvalidValue;
 }
 
@@ -172,22 +184,26 @@ extern "C" mcd_status mc_design_eval_noalloc(int device, const mcd_problem* prob
     if (N > (1ull << 62) / static_cast<uint64_t>(d)) return MCD_EINVAL;
     if (cudaSetDevice(device) != cudaSuccess) return MCD_ECUDA;
     // Set-up on the first call for this device: the device address of the
-    // static scratch array (host code may not use the array's name directly).
+    // static scratch array (host code may not use the array's name directly)
+    // and the SM count.
     NoAllocScratch* sc;
+    int sms;
     {
         std::lock_guard<std::mutex> lk(g_scratch_mu);
         if (!g_scratch_ptr[device]) {
             void* ptr = nullptr;
-            if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+            int count = 0;
+            if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr ||
+                cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
                 cudaGetLastError();
                 return MCD_ECUDA;
             }
+            g_sm_count[device] = std::max(count, 1);
             g_scratch_ptr[device] = static_cast<NoAllocScratch*>(ptr);
         }
         sc = g_scratch_ptr[device];
+        sms = g_sm_count[device];
     }
-    cudaDeviceProp prop;
-    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return MCD_ECUDA;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (J == 0) return MCD_OK;
     // the counters must start at zero; the keys of this call replace the last call's
@@ -213,7 +229,7 @@ extern "C" mcd_status mc_design_eval_noalloc(int device, const mcd_problem* prob
         const double cost = 17.0 * d + 0.5 * d * (d + 1) + 6.0;
         const int64_t T = std::max<int64_t>(1, std::llround(32768.0 / cost / g)) * g * 256;
         const int64_t tpd = static_cast<int64_t>((N + T - 1) / T);
-        if (dispatch_noalloc<1>(d, P, sc, J, N, T, tpd, prop.multiProcessorCount, s) != cudaSuccess) return MCD_ECUDA;
+        if (dispatch_noalloc<1>(d, P, sc, J, N, T, tpd, sms, device, s) != cudaSuccess) return MCD_ECUDA;
     }
     noalloc_finalize_kernel<<<(J + 127) / 128, 128, 0, s>>>(sc, J, d, N, prob->mu, prob->b, prob->region, hits, p, se);
     if (cudaGetLastError() != cudaSuccess) return MCD_ECUDA;

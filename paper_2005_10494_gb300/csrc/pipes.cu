@@ -13,6 +13,7 @@
 // clock = (the blocks' operations on one SM) / (last end - first start on
 // that SM), a figure that does not depend on the clock frequency.
 #include <cstdint>
+#include <cstring>
 
 #include <cuda_runtime.h>
 
@@ -58,8 +59,16 @@ __device__ __forceinline__ void ffma_ring(float* f, int n, float c) {
         asm volatile("fma.rn.f32 %0, %0, %1, %2;" : "+f"(f[i]) : "f"(c), "f"(f[(i + 1) % n]));
 }
 
+// The packed form: one fma.rn.f32x2 does two FP32 FMAs on a register pair.
+__device__ __forceinline__ void ffma2_ring(unsigned long long* f, int n, unsigned long long c) {
+#pragma unroll
+    for (int i = 0; i < n; ++i)
+        asm volatile("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(f[i]) : "l"(c), "l"(f[(i + 1) % n]));
+}
+
 // Throughput kernel for instruction class OP; every step is kChains
-// instructions of that class (MCD_PIPE_MIXED: half FFMA, half LOP3;
+// instructions of that class (MCD_PIPE_FFMA2 counts packed instructions,
+// two FMAs each; MCD_PIPE_MIXED: half FFMA, half LOP3;
 // MCD_PIPE_PHILOX: two calls' rounds 2..10, counted as their 36 wide
 // multiplies).
 template <int OP>
@@ -116,6 +125,19 @@ pipe_kernel(int iters, uint32_t m, float c, PipeKeys keys, uint32_t* __restrict_
         for (int k = 0; k < iters; ++k) ffma_ring(f, kChains, c);
 #pragma unroll
         for (int i = 0; i < kChains; ++i) fold ^= __float_as_uint(f[i]);
+    } else if constexpr (OP == MCD_PIPE_FFMA2) {
+        unsigned long long f[kChains];
+        const float c2[2] = {c, c};
+        unsigned long long cc;
+        memcpy(&cc, c2, 8);
+#pragma unroll
+        for (int i = 0; i < kChains; ++i) {
+            const float v[2] = {static_cast<float>(gid & 1023u) * 1e-3f + i, static_cast<float>(i) - 0.5f};
+            memcpy(&f[i], v, 8);
+        }
+        for (int k = 0; k < iters; ++k) ffma2_ring(f, kChains, cc);
+#pragma unroll
+        for (int i = 0; i < kChains; ++i) fold ^= static_cast<uint32_t>(f[i]) ^ static_cast<uint32_t>(f[i] >> 32);
     } else if constexpr (OP == MCD_PIPE_LDS128) {
         // warp-uniform addresses: each load is one broadcast transaction.
         // Four chains, two loads each per step (every load writes four
@@ -216,6 +238,7 @@ cudaError_t launch_pipe(int op, int iters, int blocks, uint32_t m, float c, uint
         case MCD_PIPE_MAD_LO: pipe_kernel<MCD_PIPE_MAD_LO><<<g, b, 0, s>>>(iters, m, c, keys, sink, t0, t1, smid); break;
         case MCD_PIPE_LOP3: pipe_kernel<MCD_PIPE_LOP3><<<g, b, 0, s>>>(iters, m, c, keys, sink, t0, t1, smid); break;
         case MCD_PIPE_FFMA: pipe_kernel<MCD_PIPE_FFMA><<<g, b, 0, s>>>(iters, m, c, keys, sink, t0, t1, smid); break;
+        case MCD_PIPE_FFMA2: pipe_kernel<MCD_PIPE_FFMA2><<<g, b, 0, s>>>(iters, m, c, keys, sink, t0, t1, smid); break;
         case MCD_PIPE_LG2: pipe_kernel<MCD_PIPE_LG2><<<g, b, 0, s>>>(iters, m, c, keys, sink, t0, t1, smid); break;
         case MCD_PIPE_SQRT: pipe_kernel<MCD_PIPE_SQRT><<<g, b, 0, s>>>(iters, m, c, keys, sink, t0, t1, smid); break;
         case MCD_PIPE_SIN: pipe_kernel<MCD_PIPE_SIN><<<g, b, 0, s>>>(iters, m, c, keys, sink, t0, t1, smid); break;

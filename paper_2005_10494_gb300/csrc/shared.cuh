@@ -9,9 +9,10 @@
 // every draw of the batch (broadcast shared loads).  A design's indicator is
 // the per-design kernel's FP32 comparison y_i > t_i, evaluated as the sign of
 // the FP32 difference t_i - y_i (an exactly equivalent test), so hit counts
-// are bit-identical to it; the gradient sums differ only in the order of
-// FP32 additions.  Draws outside the tile's range enter as y = -inf, z = 0, which
-// no region test counts and which add nothing to any sum.
+// are bit-identical to it; the gradient sums differ only in FP32 rounding
+// (the order of additions, and the sigmoid's exponent formed from that
+// difference).  Draws outside the tile's range enter as y = -inf, z = 0,
+// which no region test counts and which add nothing to any sum.
 //
 // The paper's two-layer estimator (Sec. 2.2, Eq. 7) has this form too: its
 // outer prior samples act as designs (thresholds b - S Delta_k) that share
@@ -94,14 +95,16 @@ __device__ __forceinline__ void load_row(const float* p, float* v) {
 // against this thread's first NQ designs.  y_i > t_i exactly when the FP32
 // difference t_i - y_i is negative: two unequal floats never subtract to
 // zero (gradual underflow), rounding keeps the sign, and the infinities
-// (dropped tests, draws outside the range) give +inf.  So the hit is the sign
-// bit of the or of the differences: FADDs and one or per draw instead of a
-// compare and a predicate merge per coordinate.  The draw loop is unrolled
+// (dropped tests, draws outside the range) give +inf.  Forward: the hit is
+// the sign bit of the or of the differences (FADDs and one three-input or
+// per draw instead of a compare and a predicate merge per coordinate).
+// Adjoint: the hit is a negative smallest difference, and the same minimum
+// gives the largest sigmoid exponent (below).  The draw loop is unrolled
 // (8 draws forward, 4 with the adjoint's larger bodies).
 template <int D, bool GRAD, int DPT, int NQ>
 __device__ __forceinline__ void test_draws(const float* sy, const float* sz, int nb, const float (&t)[DPT][D],
-                                           const float (&tsc)[DPT][GRAD ? D : 1], float hl2e, uint32_t (&cnt)[DPT],
-                                           float (&A)[DPT][GRAD ? D : 1], float (&G)[DPT][GRAD ? D : 1]) {
+                                           float nhl2e, uint32_t (&cnt)[DPT], float (&A)[DPT][GRAD ? D : 1],
+                                           float (&G)[DPT][GRAD ? D : 1]) {
     constexpr int DP = SharedShape<D, GRAD>::kDP;
     constexpr int kUnroll = GRAD ? 4 : 8;
 #pragma unroll kUnroll
@@ -112,24 +115,47 @@ __device__ __forceinline__ void test_draws(const float* sy, const float* sz, int
         if constexpr (GRAD) load_row<DP>(sz + dn * DP, zz);
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            uint32_t sgn = 0u;
+            if constexpr (!GRAD) {
+                uint32_t sgn = 0u;
 #pragma unroll
-            for (int i = 0; i < D; ++i) sgn |= __float_as_uint(__fsub_rn(t[q][i], y[i]));
-            const uint32_t hit = sgn >> 31;
-            cnt[q] += hit;
-            if constexpr (GRAD) {
-                const float hv = hit ? 1.0f : 0.0f;
+                for (int i = 0; i < D; ++i) sgn |= __float_as_uint(__fsub_rn(t[q][i], y[i]));
+                cnt[q] += sgn >> 31;
+            } else {
+                float dif[D], dmin = INFINITY;
 #pragma unroll
-                for (int i = 0; i < D; ++i) A[q][i] = fmadd(hv, zz[i], A[q][i]);
-                if (hl2e != 0.0f) {
-                    float keep[D], prod = 1.0f;
+                for (int i = 0; i < D; ++i) {
+                    dif[i] = __fsub_rn(t[q][i], y[i]);
+                    dmin = fminf(dmin, dif[i]);
+                }
+                const bool hit = dmin < 0.0f;
+                cnt[q] += hit ? 1u : 0u;
+                // sum A over the hits (adding z, or nothing, as the FMA
+                // with a 0/1 factor does)
+                if (hit) {
 #pragma unroll
-                    for (int i = 0; i < D; ++i) {
-                        keep[i] = smooth_keep(y[i], t[q][i], tsc[q][i], hl2e, 0.0);
-                        prod *= keep[i];
+                    for (int i = 0; i < D; ++i) A[q][i] = __fadd_rn(A[q][i], zz[i]);
+                }
+                if (nhl2e != 0.0f) {
+                    // x_i = (y_i - t_i) log2(e) / h = (t_i - y_i) nhl2e, the
+                    // exponent of the sigmoid; the largest is dmin nhl2e
+                    // (nhl2e < 0, rounding is monotone).  A draw adds
+                    // exactly zero to every G_i when all x_i < -25 (2^x_i <
+                    // 2^-25 vanishes in 1 + 2^x_i, so every keep_i = 1) or
+                    // some x_k >= 128 (2^x_k = inf, so keep_k = 0 and the
+                    // product is 0); the exponentials are taken only when
+                    // some lane of the warp has a draw between, so the sums
+                    // are those of the full loop.
+                    const float xm = dmin * nhl2e;
+                    if (__any_sync(0xffffffffu, xm >= -25.0f && xm < 128.0f)) {
+                        float keep[D], prod = 1.0f;
+#pragma unroll
+                        for (int i = 0; i < D; ++i) {
+                            keep[i] = rcp_approx(1.0f + ex2_approx(dif[i] * nhl2e));
+                            prod *= keep[i];
+                        }
+#pragma unroll
+                        for (int i = 0; i < D; ++i) G[q][i] = fmadd(prod, 1.0f - keep[i], G[q][i]);
                     }
-#pragma unroll
-                    for (int i = 0; i < D; ++i) G[q][i] = fmadd(prod, 1.0f - keep[i], G[q][i]);
                 }
             }
         }
@@ -167,7 +193,7 @@ __global__ void __launch_bounds__(kSharedThreads) shared_kernel(const __grid_con
         // and their thresholds; a missing design gets t = +inf (never a hit)
         const int nq = static_cast<int>((tl.list_cnt + blockDim.x - 1) / blockDim.x);   // block-uniform
         int dsg[DPT];
-        float t[DPT][D], tsc[DPT][GRAD ? D : 1];
+        float t[DPT][D];
 #pragma unroll
         for (int q = 0; q < DPT; ++q) {
             const uint32_t li = threadIdx.x + q * blockDim.x;
@@ -178,8 +204,6 @@ __global__ void __launch_bounds__(kSharedThreads) shared_kernel(const __grid_con
                 const double tt = dsg[q] >= 0 ? P.b[vo + i] - P.mu[vo + i] : 0.0;
                 if (dsg[q] >= 0 && tt != tt) set_status(P.status, MCD_ENAN, dsg[q]);
                 t[q][i] = dsg[q] >= 0 ? static_cast<float>(tt) : INFINITY;
-                if constexpr (GRAD)
-                    tsc[q][i] = (P.hinv_log2e != 0.0f && dsg[q] >= 0) ? static_cast<float>(tt) * P.hinv_log2e : 0.0f;
             }
         }
         __syncthreads();                              // sL complete
@@ -203,7 +227,7 @@ __global__ void __launch_bounds__(kSharedThreads) shared_kernel(const __grid_con
         }
 #pragma unroll
         for (int i = 0; i < (GRAD ? D : 1); ++i) bsum[i] = 0.0f;
-        const float hl2e = GRAD ? P.hinv_log2e : 0.0f;
+        const float nhl2e = GRAD ? -P.hinv_log2e : 0.0f;
 
         for (uint32_t g0 = 0; g0 < ngroups; g0 += blockDim.x) {
             const uint32_t gi = g0 + threadIdx.x;
@@ -214,12 +238,12 @@ __global__ void __launch_bounds__(kSharedThreads) shared_kernel(const __grid_con
             const int nb = static_cast<int>(min(static_cast<uint32_t>(SS::kBD), (ngroups - g0) * S::kG));
             // nq is block-uniform: one branch per batch picks the loop for
             // exactly nq designs per thread
-            if (nq >= DPT) test_draws<D, GRAD, DPT, DPT>(sy, sz, nb, t, tsc, hl2e, cnt, A, G);
+            if (nq >= DPT) test_draws<D, GRAD, DPT, DPT>(sy, sz, nb, t, nhl2e, cnt, A, G);
             else if constexpr (DPT > 1) {
-                if (nq == 1) test_draws<D, GRAD, DPT, 1>(sy, sz, nb, t, tsc, hl2e, cnt, A, G);
+                if (nq == 1) test_draws<D, GRAD, DPT, 1>(sy, sz, nb, t, nhl2e, cnt, A, G);
                 else if constexpr (DPT > 2) {
-                    if (nq == 2) test_draws<D, GRAD, DPT, 2>(sy, sz, nb, t, tsc, hl2e, cnt, A, G);
-                    else if constexpr (DPT > 3) test_draws<D, GRAD, DPT, 3>(sy, sz, nb, t, tsc, hl2e, cnt, A, G);
+                    if (nq == 2) test_draws<D, GRAD, DPT, 2>(sy, sz, nb, t, nhl2e, cnt, A, G);
+                    else if constexpr (DPT > 3) test_draws<D, GRAD, DPT, 3>(sy, sz, nb, t, nhl2e, cnt, A, G);
                 }
             }
             __syncthreads();                          // the next batch rewrites sy / sz

@@ -215,6 +215,14 @@ struct RunMax {
     }
 };
 
+// Element types of the grids: FP64 values are handled as their bit patterns
+// (conversions and argmax keys are integer operations); FP32 values are
+// read and written as they are, and their argmax keys are those of the
+// exactly converted FP64 value.
+template <typename Elem> struct GridWord;
+template <> struct GridWord<double> { using W = unsigned long long; };
+template <> struct GridWord<float> { using W = float; };
+
 // Fast FP64 -> FP32 for exponents 897..1150 (the FP32 normal range): one
 // funnel shift moves exponent and mantissa together, one subtraction
 // rebiases, the sign is or-ed back; the result truncates like d2f_bits.
@@ -260,15 +268,69 @@ __device__ __forceinline__ void store_pair(float (*tile)[SCP], int rr, int m, fl
 // before any value is converted.  Positions outside the grid hold 1.0: their
 // weight in every stencil that reads them is zero, and a finite value keeps
 // 0 * x = 0.
+// FP32 grid: pairs of floats (one 8-byte load with VEC) straight into the
+// tile, all loads of the batch in flight before the first store; raw argmax
+// keys from the exact FP64 value.  Positions outside the grid hold 1.0.
 template <int R, bool RAW, bool VEC, int K0, int K1, int SR, int SCP>
-__device__ __forceinline__ void stage_rows(const unsigned long long* __restrict__ V, int g1, int g2, int r0, int c0,
-                                           float (*tile)[SCP], RunMax& raw) {
+__device__ __forceinline__ void stage_rows_f32(const float* __restrict__ V, int g1, int g2, int r0, int c0,
+                                               float (*tile)[SCP], RunMax& raw) {
     constexpr int E = (R + 1) / 2 * 2;
     constexpr int NPR = (kColsPerBlock + 2 * E) / 2;        // pairs per staged row
     constexpr int PPL = (NPR + 31) / 32;                    // pair slots per lane
     constexpr int NK = K1 - K0;
-    constexpr unsigned long long kOne = 0x3ff0000000000000ull;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2 v[NK][PPL];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        const int rr = warp + 8 * (K0 + k);
+        const int gr = r0 - R + rr;
+        const bool row_in = rr < SR && gr >= 0 && gr < g1;
+#pragma unroll
+        for (int p = 0; p < PPL; ++p) {
+            const int m = lane + 32 * p;
+            const int gc = c0 - E + 2 * m;
+            v[k][p] = make_float2(1.0f, 1.0f);
+            if (row_in && m < NPR) {
+                const float* q = V + static_cast<int64_t>(gr) * g2 + gc;
+                if constexpr (VEC) {
+                    if (gc >= 0 && gc < g2) v[k][p] = __ldg(reinterpret_cast<const float2*>(q));
+                } else {
+                    if (gc >= 0 && gc < g2) v[k][p].x = __ldg(q);
+                    if (gc + 1 >= 0 && gc + 1 < g2) v[k][p].y = __ldg(q + 1);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        const int rr = warp + 8 * (K0 + k);
+        const int gr = r0 - R + rr;
+#pragma unroll
+        for (int p = 0; p < PPL; ++p) {
+            const int m = lane + 32 * p;
+            const int gc = c0 - E + 2 * m;
+            store_pair<R, E, NPR, SR, SCP>(tile, rr, m, v[k][p].x, v[k][p].y);
+            if constexpr (RAW) {
+                if (rr < SR && m < NPR && rr >= R && rr < R + kRowsPerBlock && gr >= 0 && gr < g1) {
+                    if (gc >= c0 && gc < c0 + kColsPerBlock && gc < g2)
+                        raw.add(v[k][p].x, f2d_bits(v[k][p].x), static_cast<long long>(gr) * g2 + gc);
+                    if (gc + 1 >= c0 && gc + 1 < c0 + kColsPerBlock && gc + 1 < g2)
+                        raw.add(v[k][p].y, f2d_bits(v[k][p].y), static_cast<long long>(gr) * g2 + gc + 1);
+                }
+            }
+        }
+    }
+}
+
+template <int R, bool RAW, bool VEC, int K0, int K1, int SR, int SCP>
+__device__ __forceinline__ void stage_rows_f64(const unsigned long long* __restrict__ V, int g1, int g2, int r0,
+                                               int c0, float (*tile)[SCP], RunMax& raw) {
+    constexpr int E = (R + 1) / 2 * 2;
+    constexpr int NPR = (kColsPerBlock + 2 * E) / 2;        // pairs per staged row
+    constexpr int PPL = (NPR + 31) / 32;                    // pair slots per lane
+    constexpr int NK = K1 - K0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr unsigned long long kOne = 0x3ff0000000000000ull;
     unsigned long long b0[NK][PPL], b1[NK][PPL];
 #pragma unroll
     for (int k = 0; k < NK; ++k) {
@@ -332,6 +394,13 @@ __device__ __forceinline__ void stage_rows(const unsigned long long* __restrict_
     }
 }
 
+template <int R, bool RAW, bool VEC, int K0, int K1, int SR, int SCP, typename Elem>
+__device__ __forceinline__ void stage_rows(const typename GridWord<Elem>::W* __restrict__ V, int g1, int g2, int r0,
+                                           int c0, float (*tile)[SCP], RunMax& raw) {
+    if constexpr (sizeof(Elem) == 4) stage_rows_f32<R, RAW, VEC, K0, K1, SR, SCP>(V, g1, g2, r0, c0, tile, raw);
+    else stage_rows_f64<R, RAW, VEC, K0, K1, SR, SCP>(V, g1, g2, r0, c0, tile, raw);
+}
+
 // Shape constants of the 2-D kernels for reach R.
 template <int R>
 struct Tile2D {
@@ -352,10 +421,10 @@ constexpr int kWarps2D = 8;           // argmax candidates per 2-D tile (one per
 // edge), one per thread, with their class stencils; then the tile's argmax
 // candidates (smoothed, and raw when RAW), one per warp, at slot `slot` of
 // scenario s.
-template <int R, bool RAW>
+template <int R, bool RAW, typename Elem>
 __device__ __forceinline__ void tile_outputs(float (*tile)[Tile2D<R>::SCP], int g1, int g2, int s, int r0, int c0,
                                              const float* __restrict__ w32, const float* __restrict__ wint,
-                                             unsigned long long* __restrict__ out, int nb, int slot,
+                                             typename GridWord<Elem>::W* __restrict__ out, int nb, int slot,
                                              unsigned long long* part_v, long long* part_i,
                                              unsigned long long* rpart_v, long long* rpart_i,
                                              RunMax& raw) {
@@ -364,7 +433,7 @@ __device__ __forceinline__ void tile_outputs(float (*tile)[Tile2D<R>::SCP], int 
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int orow = r0 + 4 * ty, ocol = c0 + 4 * tx;       // first output of this thread
     const int ncls = (R + 1) * (R + 1);
-    unsigned long long* O = out ? out + static_cast<int64_t>(s) * g1 * g2 : nullptr;
+    typename GridWord<Elem>::W* O = out ? out + static_cast<int64_t>(s) * g1 * g2 : nullptr;
     float best = -INFINITY;
     // Interior stencil of every output of the patch.  The interior window is
     // symmetric (tricube product weights, monomial basis), so its stencil
@@ -413,27 +482,40 @@ __device__ __forceinline__ void tile_outputs(float (*tile)[Tile2D<R>::SCP], int 
 #pragma unroll
         for (int j = 0; j < 4; ++j) col_int[j] = ocol + j >= R && ocol + j <= g2 - 1 - R;
         const bool all_cols = col_int[0] && col_int[3];
-        const bool vec_out = (g2 % 2) == 0 && (reinterpret_cast<uintptr_t>(O) & 15u) == 0;
+        // 16-byte stores: pairs of doubles (even row length) or four floats
+        // (row length a multiple of 4), from a 16-byte aligned output
+        const bool vec_out = (g2 % (sizeof(Elem) == 4 ? 4 : 2)) == 0 && (reinterpret_cast<uintptr_t>(O) & 15u) == 0;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const bool row_int = orow + i >= R && orow + i <= g1 - 1 - R;
             const int64_t idx0 = static_cast<int64_t>(orow + i) * g2 + ocol;
-            unsigned long long o[4];
-            bool bad = false;
+            if constexpr (sizeof(Elem) == 4) {
+                if (O && row_int) {
+                    if (vec_out && all_cols) {
+                        *reinterpret_cast<float4*>(O + idx0) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+                    } else {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) o[j] = f2d_fast(acc[i][j], bad);
-            if (__any_sync(0xffffffffu, bad)) {
+                        for (int j = 0; j < 4; ++j) if (col_int[j]) O[idx0 + j] = acc[i][j];
+                    }
+                }
+            } else {
+                unsigned long long o[4];
+                bool bad = false;
 #pragma unroll
-                for (int j = 0; j < 4; ++j) o[j] = f2d_bits(acc[i][j]);
-            }
-            if (O && row_int) {
-                if (vec_out && all_cols) {
-                    ulonglong2* dst = reinterpret_cast<ulonglong2*>(O + idx0);
-                    dst[0] = make_ulonglong2(o[0], o[1]);
-                    dst[1] = make_ulonglong2(o[2], o[3]);
-                } else {
+                for (int j = 0; j < 4; ++j) o[j] = f2d_fast(acc[i][j], bad);
+                if (__any_sync(0xffffffffu, bad)) {
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) if (col_int[j]) O[idx0 + j] = o[j];
+                    for (int j = 0; j < 4; ++j) o[j] = f2d_bits(acc[i][j]);
+                }
+                if (O && row_int) {
+                    if (vec_out && all_cols) {
+                        ulonglong2* dst = reinterpret_cast<ulonglong2*>(O + idx0);
+                        dst[0] = make_ulonglong2(o[0], o[1]);
+                        dst[1] = make_ulonglong2(o[2], o[3]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) if (col_int[j]) O[idx0 + j] = o[j];
+                    }
                 }
             }
 #pragma unroll
@@ -477,7 +559,10 @@ __device__ __forceinline__ void tile_outputs(float (*tile)[Tile2D<R>::SCP], int 
                 for (int dy = 0; dy < T; ++dy)
                     a = fmaf(__ldg(&w[dx * T + dy]), tile[r - r0 + dx][c - c0 + dy], a);
             const long long idx = static_cast<long long>(r) * g2 + c;
-            if (O) O[idx] = f2d_bits(a);
+            if (O) {
+                if constexpr (sizeof(Elem) == 4) O[idx] = a;
+                else O[idx] = f2d_bits(a);
+            }
             if (a > eb_v || (a == eb_v && idx < eb_i)) { eb_v = a; eb_i = idx; }
         }
     }
@@ -530,33 +615,34 @@ __device__ __forceinline__ void tile_outputs(float (*tile)[Tile2D<R>::SCP], int 
 // (stage_rows, in three batches of rows, each with all its loads in flight
 // at once), then tile_outputs.  VEC: g2 even and the input 16-byte aligned
 // (pairs of doubles per load).
-template <int R, bool RAW, bool VEC>
-__global__ void __launch_bounds__(256, 4) smooth2d_kernel(const unsigned long long* __restrict__ val, int g1, int g2,
-                                                       const float* __restrict__ w32, const float* __restrict__ wint,
-                                                       unsigned long long* __restrict__ out,
+template <int R, bool RAW, bool VEC, typename Elem>
+__global__ void __launch_bounds__(256, 4) smooth2d_kernel(const typename GridWord<Elem>::W* __restrict__ val, int g1,
+                                                       int g2, const float* __restrict__ w32,
+                                                       const float* __restrict__ wint,
+                                                       typename GridWord<Elem>::W* __restrict__ out,
                                                        unsigned long long* part_v, long long* part_i,
                                                        unsigned long long* rpart_v, long long* rpart_i) {
     using TS = Tile2D<R>;
     __shared__ __align__(16) float tile[TS::SR][TS::SCP];
     const int s = blockIdx.z;
     const int r0 = blockIdx.y * kRowsPerBlock, c0 = blockIdx.x * kColsPerBlock;
-    const unsigned long long* V = val + static_cast<int64_t>(s) * g1 * g2;
+    const typename GridWord<Elem>::W* V = val + static_cast<int64_t>(s) * g1 * g2;
     RunMax raw;
     raw.init();
     static_assert(TS::RPW == 5, "staging batches assume 5 rows per warp");
-    stage_rows<R, RAW, VEC, 0, 2, TS::SR, TS::SCP>(V, g1, g2, r0, c0, tile, raw);
-    stage_rows<R, RAW, VEC, 2, 4, TS::SR, TS::SCP>(V, g1, g2, r0, c0, tile, raw);
-    stage_rows<R, RAW, VEC, 4, 5, TS::SR, TS::SCP>(V, g1, g2, r0, c0, tile, raw);
+    stage_rows<R, RAW, VEC, 0, 2, TS::SR, TS::SCP, Elem>(V, g1, g2, r0, c0, tile, raw);
+    stage_rows<R, RAW, VEC, 2, 4, TS::SR, TS::SCP, Elem>(V, g1, g2, r0, c0, tile, raw);
+    stage_rows<R, RAW, VEC, 4, 5, TS::SR, TS::SCP, Elem>(V, g1, g2, r0, c0, tile, raw);
     __syncthreads();
-    tile_outputs<R, RAW>(tile, g1, g2, s, r0, c0, w32, wint, out, gridDim.x * gridDim.y,
-                         blockIdx.y * gridDim.x + blockIdx.x, part_v, part_i, rpart_v, rpart_i, raw);
+    tile_outputs<R, RAW, Elem>(tile, g1, g2, s, r0, c0, w32, wint, out, gridDim.x * gridDim.y,
+                            blockIdx.y * gridDim.x + blockIdx.x, part_v, part_i, rpart_v, rpart_i, raw);
 }
 
 // 1-D stencil along a line of n points.
-template <int R>
-__global__ void __launch_bounds__(256) smooth1d_kernel(const unsigned long long* __restrict__ val, int n,
+template <int R, typename Elem>
+__global__ void __launch_bounds__(256) smooth1d_kernel(const typename GridWord<Elem>::W* __restrict__ val, int n,
                                                        const float* __restrict__ w32,
-                                                       unsigned long long* __restrict__ out,
+                                                       typename GridWord<Elem>::W* __restrict__ out,
                                                        unsigned long long* part_v, long long* part_i,
                                                        unsigned long long* rpart_v, long long* rpart_i) {
     constexpr int T = 2 * R + 1;
@@ -565,15 +651,21 @@ __global__ void __launch_bounds__(256) smooth1d_kernel(const unsigned long long*
     __shared__ long long si[8];
     const int s = blockIdx.y;
     const int c0 = blockIdx.x * kLine;
-    const unsigned long long* V = val + static_cast<int64_t>(s) * n;
+    const typename GridWord<Elem>::W* V = val + static_cast<int64_t>(s) * n;
     unsigned long long raw_v = 0;
     long long raw_i = -1;
     for (int q = threadIdx.x; q < kLine + 2 * R; q += blockDim.x) {
         const int g = c0 - R + q;
         float x = 0.0f;
         if (g >= 0 && g < n) {
-            const unsigned long long bits = __ldg(&V[g]);
-            x = d2f_bits(bits);
+            unsigned long long bits;
+            if constexpr (sizeof(Elem) == 4) {
+                x = __ldg(&V[g]);
+                bits = f2d_bits(x);
+            } else {
+                bits = __ldg(&V[g]);
+                x = d2f_bits(bits);
+            }
             if (q >= R && q < R + kLine) amax_value(raw_v, raw_i, bits, g);
         }
         line[q] = x;
@@ -589,7 +681,10 @@ __global__ void __launch_bounds__(256) smooth1d_kernel(const unsigned long long*
 #pragma unroll
         for (int dx = 0; dx < T; ++dx) acc = fmaf(__ldg(&w[dx]), line[q + dx], acc);
         const unsigned long long o = f2d_bits(acc);
-        if (out) out[static_cast<int64_t>(s) * n + c] = o;
+        if (out) {
+            if constexpr (sizeof(Elem) == 4) out[static_cast<int64_t>(s) * n + c] = acc;
+            else out[static_cast<int64_t>(s) * n + c] = o;
+        }
         amax_value(best_v, best_i, o, c);
     }
     const int nb = gridDim.x;
@@ -602,9 +697,10 @@ __global__ void __launch_bounds__(256) smooth1d_kernel(const unsigned long long*
 
 // One block per scenario: fold its argmax candidates (largest key, then
 // lowest index, so the order of the candidates does not matter).
+template <typename Elem>
 __global__ void argmax_kernel(int nb, const unsigned long long* part_v, const long long* part_i,
                               const unsigned long long* rpart_v, const long long* rpart_i, int64_t* idx,
-                              double* v, int64_t* ridx, double* rv) {
+                              Elem* v, int64_t* ridx, Elem* rv) {
     __shared__ unsigned long long sv[8];
     __shared__ long long si[8];
     const int s = blockIdx.x;
@@ -615,7 +711,7 @@ __global__ void argmax_kernel(int nb, const unsigned long long* part_v, const lo
     block_amax(bv, bi, sv, si);
     if (threadIdx.x == 0) {
         if (idx) idx[s] = bi;
-        if (v) v[s] = bi >= 0 ? __longlong_as_double(static_cast<long long>(key_bits(bv))) : NAN;
+        if (v) v[s] = static_cast<Elem>(bi >= 0 ? __longlong_as_double(static_cast<long long>(key_bits(bv))) : NAN);
     }
     if (!ridx && !rv) return;
     __syncthreads();
@@ -626,7 +722,7 @@ __global__ void argmax_kernel(int nb, const unsigned long long* part_v, const lo
     block_amax(bv, bi, sv, si);
     if (threadIdx.x == 0) {
         if (ridx) ridx[s] = bi;
-        if (rv) rv[s] = bi >= 0 ? __longlong_as_double(static_cast<long long>(key_bits(bv))) : NAN;
+        if (rv) rv[s] = static_cast<Elem>(bi >= 0 ? __longlong_as_double(static_cast<long long>(key_bits(bv))) : NAN);
     }
 }
 
@@ -666,12 +762,16 @@ size_t smooth_candidate_count(int n_scen, int g1, int g2) {
     return 2 * static_cast<size_t>(n_scen) * candidates_per_scen(g1, g2);
 }
 
+namespace {
+
 // wbuf / wbuf32: stencil weights (smooth_weight_count() each); part_val /
 // part_idx: smooth_candidate_count() argmax candidates.
-cudaError_t smooth_argmax(int n_scen, int g1, int g2, const double* value, double bandwidth,
-                          int degree, double* smoothed, int64_t* argmax_idx, double* argmax_val,
-                          int64_t* raw_idx, double* raw_val, double* wbuf, float* wbuf32,
-                          double* part_val, int64_t* part_idx, DevStatus* status, cudaStream_t stream) {
+template <typename Elem>
+cudaError_t smooth_argmax_t(int n_scen, int g1, int g2, const Elem* value, double bandwidth, int degree, Elem* smoothed,
+                            int64_t* argmax_idx, Elem* argmax_val, int64_t* raw_idx, Elem* raw_val, double* wbuf,
+                            float* wbuf32, double* part_val, int64_t* part_idx, DevStatus* status,
+                            cudaStream_t stream) {
+    using W = typename GridWord<Elem>::W;
     const int R = reach_of(bandwidth);
     const bool two_d = (g1 > 1 && g2 > 1);
     const int ncls = (R + 1) * (R + 1);
@@ -687,19 +787,20 @@ cudaError_t smooth_argmax(int n_scen, int g1, int g2, const double* value, doubl
     long long* pi = reinterpret_cast<long long*>(part_idx);
     unsigned long long* rpv = pv + static_cast<size_t>(n_scen) * ncand;
     long long* rpi = pi + static_cast<size_t>(n_scen) * ncand;
-    const unsigned long long* vb = reinterpret_cast<const unsigned long long*>(value);
-    unsigned long long* ob = reinterpret_cast<unsigned long long*>(smoothed);
+    const W* vb = reinterpret_cast<const W*>(value);
+    W* ob = reinterpret_cast<W*>(smoothed);
     if (two_d) {
         dim3 grid((g2 + kColsPerBlock - 1) / kColsPerBlock, (g1 + kRowsPerBlock - 1) / kRowsPerBlock, n_scen);
         const bool raw = raw_idx || raw_val;
-        // pairs of doubles per load when every row starts on a 16-byte boundary
-        const bool vec = (g2 % 2) == 0 && (reinterpret_cast<uintptr_t>(value) & 15u) == 0;
+        // one 16-byte (FP64) or 8-byte (FP32) load per pair of values when
+        // every row starts on such a boundary
+        const bool vec = (g2 % 2) == 0 && (reinterpret_cast<uintptr_t>(value) & (2 * sizeof(Elem) - 1)) == 0;
         const float* wint = wbuf32 + static_cast<size_t>(kClassSlots) * kMaxTaps;
         const int key = (R - 1) * 4 + (raw ? 2 : 0) + (vec ? 1 : 0);
         switch (key) {
 #define MCD_SMOOTH2D(RR, RAW, VEC) \
             case (RR - 1) * 4 + (RAW ? 2 : 0) + (VEC ? 1 : 0): \
-                smooth2d_kernel<RR, RAW, VEC><<<grid, 256, 0, stream>>>(vb, g1, g2, wbuf32, wint, ob, pv, pi, rpv, rpi); \
+                smooth2d_kernel<RR, RAW, VEC, Elem><<<grid, 256, 0, stream>>>(vb, g1, g2, wbuf32, wint, ob, pv, pi, rpv, rpi); \
                 break;
             MCD_SMOOTH2D(1, false, false) MCD_SMOOTH2D(1, false, true) MCD_SMOOTH2D(1, true, false) MCD_SMOOTH2D(1, true, true)
             MCD_SMOOTH2D(2, false, false) MCD_SMOOTH2D(2, false, true) MCD_SMOOTH2D(2, true, false) MCD_SMOOTH2D(2, true, true)
@@ -710,14 +811,32 @@ cudaError_t smooth_argmax(int n_scen, int g1, int g2, const double* value, doubl
     } else {
         dim3 grid(nb, n_scen);
         const int n = g1 * g2;
-        if (R == 1) smooth1d_kernel<1><<<grid, 256, 0, stream>>>(vb, n, wbuf32, ob, pv, pi, rpv, rpi);
-        else if (R == 2) smooth1d_kernel<2><<<grid, 256, 0, stream>>>(vb, n, wbuf32, ob, pv, pi, rpv, rpi);
-        else smooth1d_kernel<3><<<grid, 256, 0, stream>>>(vb, n, wbuf32, ob, pv, pi, rpv, rpi);
+        if (R == 1) smooth1d_kernel<1, Elem><<<grid, 256, 0, stream>>>(vb, n, wbuf32, ob, pv, pi, rpv, rpi);
+        else if (R == 2) smooth1d_kernel<2, Elem><<<grid, 256, 0, stream>>>(vb, n, wbuf32, ob, pv, pi, rpv, rpi);
+        else smooth1d_kernel<3, Elem><<<grid, 256, 0, stream>>>(vb, n, wbuf32, ob, pv, pi, rpv, rpi);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    argmax_kernel<<<n_scen, 256, 0, stream>>>(ncand, pv, pi, rpv, rpi, argmax_idx, argmax_val, raw_idx, raw_val);
+    argmax_kernel<Elem><<<n_scen, 256, 0, stream>>>(ncand, pv, pi, rpv, rpi, argmax_idx, argmax_val, raw_idx, raw_val);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t smooth_argmax(int n_scen, int g1, int g2, const double* value, double bandwidth,
+                          int degree, double* smoothed, int64_t* argmax_idx, double* argmax_val,
+                          int64_t* raw_idx, double* raw_val, double* wbuf, float* wbuf32,
+                          double* part_val, int64_t* part_idx, DevStatus* status, cudaStream_t stream) {
+    return smooth_argmax_t<double>(n_scen, g1, g2, value, bandwidth, degree, smoothed, argmax_idx, argmax_val,
+                                   raw_idx, raw_val, wbuf, wbuf32, part_val, part_idx, status, stream);
+}
+
+cudaError_t smooth_argmax_f32(int n_scen, int g1, int g2, const float* value, double bandwidth,
+                              int degree, float* smoothed, int64_t* argmax_idx, float* argmax_val,
+                              int64_t* raw_idx, float* raw_val, double* wbuf, float* wbuf32,
+                              double* part_val, int64_t* part_idx, DevStatus* status, cudaStream_t stream) {
+    return smooth_argmax_t<float>(n_scen, g1, g2, value, bandwidth, degree, smoothed, argmax_idx, argmax_val,
+                                  raw_idx, raw_val, wbuf, wbuf32, part_val, part_idx, status, stream);
 }
 
 }  // namespace mcd

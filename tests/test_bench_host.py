@@ -101,3 +101,45 @@ def test_hbm_peak_reads_the_measured_figure_or_falls_back(tmp_path):
     f.write_text('{"bf16_tflops": 1979.2}')
     assert bench.hbm_peak(str(f))[0] == 6800.0
     assert bench.hbm_peak(str(tmp_path / "missing.json"))[0] == 6800.0
+
+
+def test_shared_class_counts_and_bound():
+    """The shared-draw kernel's per-draw-evaluation counts: forward d
+    differences and their sign, adjoint sums and sigmoid exponents, and the
+    sigmoid's MUFU work in the active fraction of warp-draws only."""
+    f = bench.shared_class_counts(3, False, 4)
+    assert f["ffma"] == 3 and f["alu"] == 3 and f["lds128"] == pytest.approx(0.25)
+    assert f["ex2"] == f["rcp"] == f["mul_wide"] == 0
+    g = bench.shared_class_counts(3, True, 4, active=0.5)
+    assert g["ex2"] == g["rcp"] == pytest.approx(1.5)
+    assert g["ffma"] == pytest.approx(3 + 6 + 0.5 * 12)
+    assert g["lds128"] == pytest.approx(0.5)
+    rates = {"lop3": 64.0, "ffma": 128.0, "lg2": 16.0, "sqrt": 16.0, "sin": 16.0, "cos": 16.0, "ex2": 32.0,
+             "rcp": 16.0, "lds128": 16.0}
+    b = bench.shared_pipe_bound(rates, 3, True, 4, 1.0, 152, mhz=2000.0)
+    assert b["sm_clk_per_draw"]["mufu"] == pytest.approx(3 / 32 + 3 / 16)
+    assert b["sm_clk_per_draw"]["issue"] == pytest.approx((sum(g.values()) + 0.5 * (12 + 3 + 3)) / 128)
+    slow = dict(rates, ex2=8.0, rcp=8.0)
+    assert bench.shared_pipe_bound(slow, 3, True, 4, 1.0, 152, mhz=2000.0)["binding"] == "mufu"
+    b0 = bench.shared_pipe_bound(rates, 3, True, 4, 0.0, 152, mhz=2000.0)
+    assert b0["sm_clk_per_draw"]["mufu"] == 0.0
+    assert b0["sm_clk_per_draw"]["alu"] == pytest.approx((3 + 1 + 2 + 3) / 64.0)
+    assert b0["bound_draw_evals_per_s"] > b["bound_draw_evals_per_s"]
+
+
+def test_shared_active_fraction_limits():
+    import numpy as np
+
+    import workloads
+    S = workloads.equicorrelated(3, 0.5)
+    J = 64
+    far = workloads.Problem("far", [S], [0] * J, [np.zeros(3)] * J, [np.full(3, 50.0)] * J, [100] * J, [0] * J)
+    assert bench.shared_active_fraction(far, 0.01, draws=64) == 0.0
+    wide = workloads.Problem("wide", [S], [0] * J, [np.zeros(3)] * J, [np.full(3, 1.0)] * J, [100] * J, [0] * J)
+    assert bench.shared_active_fraction(wide, 100.0, draws=64) == 1.0
+    mid = bench.shared_active_fraction(workloads.c2(n_scen=1, g1=8, g2=8, n_draws=10), 0.01, draws=256)
+    assert 0.0 < mid < 1.0
+
+
+def test_committed_shared_traffic_record_matches_the_sources():
+    assert bench.shared_traffic_record() is not None

@@ -356,6 +356,40 @@ def test_smoothing_matches_oracle(ctx, shape, bw, deg):
     np.testing.assert_array_equal(r["raw_val"].cpu().numpy(), rval_ref)
 
 
+@pytest.mark.parametrize("shape,bw,deg", [((1, 101), 3.0, 2), ((64, 64), 3.0, 2), ((37, 150), 3.0, 2),
+                                          ((5, 5), 3.0, 2), ((130, 9), 2.5, 1), ((1, 7), 4.0, 0),
+                                          ((200, 1), 3.5, 2), ((33, 257), 2.5, 2)])
+@pytest.mark.parametrize("offset", [0, 1])
+def test_smoothing_f32_grid(ctx, shape, bw, deg, offset):
+    """FP32 grids (mc_smooth_argmax_f32): on values that FP32 represents
+    exactly, the outputs equal the FP64 entry point's bit for bit (both
+    apply the stencil in FP32), and they match the oracle's least-squares
+    fit of those values within the same 2e-6; offset 1 starts the input 4
+    bytes past an 8-byte boundary (unpaired loads)."""
+    import torch
+
+    import paper_2005_10494_gb300 as pkg
+    g1, g2 = shape
+    S = 3
+    rng = np.random.default_rng(g1 * 7 + g2)
+    i, j = np.meshgrid(np.arange(g1), np.arange(g2), indexing="ij")
+    vals = np.stack([0.7 - 0.0004 * (i - g1 / 3) ** 2 - 0.0002 * (j - g2 / 2) ** 2 + rng.normal(0, 0.01, (g1, g2))
+                     for _ in range(S)]).astype(np.float32)
+    base = torch.zeros(S * g1 * g2 + 1, dtype=torch.float32, device="cuda")
+    v32 = base[offset:offset + S * g1 * g2]
+    v32.copy_(torch.as_tensor(vals.ravel()))
+    r32 = pkg.mc_smooth_argmax(ctx, v32, S, g1, g2, bandwidth=bw, degree=deg, raw=True)
+    r64 = pkg.mc_smooth_argmax(ctx, v32.double(), S, g1, g2, bandwidth=bw, degree=deg, raw=True)
+    ctx.sync_status()
+    assert r32["smoothed"].dtype == torch.float32 and r32["argmax_val"].dtype == torch.float32
+    np.testing.assert_array_equal(r32["smoothed"].double().cpu().numpy(), r64["smoothed"].cpu().numpy())
+    for k in ("argmax_idx", "argmax_val", "raw_idx", "raw_val"):
+        np.testing.assert_array_equal(r32[k].cpu().numpy().astype(np.float64), r64[k].cpu().numpy().astype(np.float64))
+    sm_ref, idx_ref, val_ref, ridx_ref, rval_ref = smooth.smooth_argmax(vals.astype(np.float64), g1, g2, bw, deg)
+    np.testing.assert_allclose(r32["smoothed"].cpu().numpy().reshape(S, g1, g2), sm_ref, rtol=0, atol=2e-6)
+    np.testing.assert_array_equal(r32["raw_idx"].cpu().numpy(), ridx_ref)
+
+
 # ------------------------------------------------------------ error paths
 def test_error_paths(ctx):
     import torch
@@ -399,6 +433,27 @@ def test_error_paths(ctx):
         pkg.mc_smooth_argmax(ctx, v, 1, 10, 10, bandwidth=5.0)
     with pytest.raises(pkg.MCDError):
         pkg.mc_smooth_argmax(ctx, v, 1, 10, 10, bandwidth=3.0, degree=3)
+
+
+def test_gradient_plan_draw_limit(ctx):
+    """A gradient plan refuses a design whose draws would put more than 2^32
+    draws into one of its 32 fixed-point batch slots (the sums could
+    overflow); smaller designs, and forward plans of any size, are planned.
+    Plans are created only (nothing is launched)."""
+    import paper_2005_10494_gb300 as pkg
+    from paper_2005_10494_gb300.binding import MCD_EINVAL
+    base = workloads.c1(n_draws=10, keys="independent").subset([3, 50])
+    for n, grad, ok in ((2 ** 38, True, False), (2 ** 36, True, True), (2 ** 38, False, True)):
+        prob = base.subset([0, 1])
+        prob.n_draws = np.array([1000, n], np.uint64)
+        dp = pkg.DeviceProblem.from_workload(prob)
+        if ok:
+            pkg.Plan(ctx, dp, grad=grad).close()
+        else:
+            with pytest.raises(pkg.MCDError) as e:
+                pkg.Plan(ctx, dp, grad=grad)
+            assert e.value.code == MCD_EINVAL and e.value.index == 1
+    ctx.sync_status()
 
 
 def test_empty_problem(ctx):
