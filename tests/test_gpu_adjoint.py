@@ -147,17 +147,21 @@ def _fd_band(out, idx, fds):
     5 SE_g, 1e-6) for the likelihood-ratio gradient; the sigmoid (pathwise)
     estimator, biased by O(h^2), within max(0.05 |g_FD|, 20 SE + 2e-3)."""
     bad, rec = [], []
+    worst = worst_s = 0.0
     for j, fd in zip(idx, fds):
         g, se = out["grad_lr"][4 * j:4 * j + 4], out["grad_se"][4 * j:4 * j + 4]
         gs = out["grad_sig"][4 * j:4 * j + 4]
         tol = np.maximum(np.maximum(0.02 * np.abs(fd), 5 * se), 1e-6)
         tol_s = np.maximum(0.05 * np.abs(fd), 20 * se + 2e-3)
+        worst = max(worst, float(np.max(np.abs(g - fd) / tol)))
+        worst_s = max(worst_s, float(np.max(np.abs(gs - fd) / tol_s)))
         rec.append({"design": int(j), "grad_lr": g.tolist(), "grad_sig": gs.tolist(), "fd": list(map(float, fd)),
                     "se": se.tolist()})
         if not (np.all(np.abs(g - fd) <= tol) and np.all(np.abs(gs - fd) <= tol_s)):
             bad.append(rec[-1])
     assert not bad, bad
-    return rec
+    return {"designs": len(idx), "max_err_over_band_lr": worst, "max_err_over_band_sigmoid": worst_s,
+            "per_design": rec}
 
 
 @pytest.fixture(scope="module")
@@ -178,13 +182,11 @@ def test_c4_full_gradients_vs_fd(c4_full):
     prob, out = c4_full
     idx = sorted(np.random.default_rng(5).choice(prob.n_design, 12, replace=False).tolist())
     fds = _fd_many([prob.params[j] for j in idx], 10, prob.structures[0])
-    rec = _fd_band(out, idx, fds)
-    report("c4 gradients vs FD of AR(1) quadrature (12 designs x 1e7 draws)", designs=len(idx), per_design=rec)
+    report("c4 gradients vs FD of AR(1) quadrature (12 designs x 1e7 draws)", **_fd_band(out, idx, fds))
 
 
 def test_c5_full_gradients_vs_fd(c5_full):
     prob, out = c5_full
     idx = workloads.c5_subsample()[:8].tolist()
     fds = _fd_many([prob.params[j] for j in idx], 20, prob.structures[0])
-    rec = _fd_band(out, idx, fds)
-    report("c5 gradients vs FD of block quadrature (8 designs x 1e7 draws)", designs=len(idx), per_design=rec)
+    report("c5 gradients vs FD of block quadrature (8 designs x 1e7 draws)", **_fd_band(out, idx, fds))
