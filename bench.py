@@ -137,27 +137,41 @@ def shared_class_counts(d, grad, dpt, active=1.0):
     """Operations per draw-evaluation of the shared-draw kernel (csrc/shared.cuh)
     for one design and one draw, by instruction class: the draw itself is
     made once per block for a whole chunk of designs, so its cost vanishes
-    per design.  Forward: d FP32 differences t_i - y_i, their or and sign
-    (d + 1 ALU) and the count add; the draw's row of y is one 16-byte load
-    per 4 coordinates, shared by the thread's dpt designs.  Adjoint: the
-    hit as a 0/1 factor and d FMAs of sum A; d FMAs of the sigmoid
-    exponents, their maximum (d - 1), the range test and the warp vote (ALU),
-    the row of z; and, in the fraction `active` of warp-draws where some
-    lane's draw is within the sigmoid's reach, per coordinate ex2, 1 + e,
-    rcp, the running product, 1 - keep and the FMA of sum G.  The sign test
-    ors the d sign words with three-input logic (ceil((d-1)/2) ops), then a
-    shift and the count add."""
+    per design.  The differences t_i - y_i go two coordinates per packed
+    FMA (floor(d/2) `ffma2`, one FP32 subtraction for an odd d); the draw's
+    row of y is one 16-byte load per 4 coordinates, shared by the thread's
+    dpt designs.  Forward: the or of the d sign words with three-input logic
+    (ceil((d-1)/2)) and the count add of the sign bit (ALU).  Adjoint: the
+    smallest difference with three-input minima (ceil((d-1)/2)), the hit
+    test, the count (select and add), the range test of the largest sigmoid
+    exponent and the warp vote (ALU); the sum A over hits (floor(d/2) packed adds, one scalar for an
+    odd d) and the exponent (one FMA); the row of z; and, in the fraction
+    `active` of warp-draws where some lane's draw is within the sigmoid's
+    reach, per coordinate the exponent, ex2, 1 + e, rcp, the running
+    product, 1 - keep and the FMA of sum G (5d FP32, 2d MUFU)."""
     rows = -(-d // 4)
-    c = {"mul_wide": 0.0, "alu": (d - 1 + 1) // 2 + 2.0, "ffma": float(d), "lg2": 0.0, "sqrt": 0.0,
-         "sin": 0.0, "cos": 0.0, "ex2": 0.0, "rcp": 0.0, "lds128": rows / float(dpt)}
+    half, odd = d // 2, d % 2
+    c = {"mul_wide": 0.0, "alu": (d - 1 + 1) // 2 + 1.0, "ffma": float(odd), "ffma2": float(half),
+         "lg2": 0.0, "sqrt": 0.0, "sin": 0.0, "cos": 0.0, "ex2": 0.0, "rcp": 0.0, "lds128": rows / float(dpt)}
     if grad:
-        c["alu"] += 1 + (d - 1) + 3
-        c["ffma"] += 2 * d
+        c["alu"] = (d - 1 + 1) // 2 + 5.0
+        c["ffma2"] += half
+        c["ffma"] += odd + 1 + active * 5 * d
         c["lds128"] += rows / float(dpt)
-        c["ffma"] += active * 4 * d
         c["ex2"] += active * d
         c["rcp"] += active * d
     return c
+
+
+def shared_fp32_flops(d, grad, active=1.0):
+    """Algorithmic FP32 flops per draw-evaluation of the shared-draw kernel
+    (FMA = 2): d differences; the adjoint adds the d sums of A, the exponent
+    FMA and, where the sigmoid is taken, per coordinate its exponent, 1 + e,
+    the product, 1 - keep and the FMA of G (6d)."""
+    f = float(d)
+    if grad:
+        f += d + 2 + 6 * d * active
+    return f
 
 
 def shared_active_fraction(prob, h, draws=1024, warp=32, seed=0):
@@ -190,9 +204,10 @@ def shared_active_fraction(prob, h, draws=1024, warp=32, seed=0):
 def shared_pipe_bound(rates, d, grad, dpt, active, sm_count, mhz=SM_MAX_MHZ):
     """The min-over-pipes bound of the shared-draw kernel (as pipe_bound)."""
     n = shared_class_counts(d, grad, dpt, active)
+    r_pk = rates.get("ffma2", rates["ffma"] / 2.0)
     clk = {
         "alu": n["alu"] / rates["lop3"],
-        "fp32": n["ffma"] / rates["ffma"],
+        "fp32": n["ffma"] / rates["ffma"] + n["ffma2"] / r_pk,
         "mufu": sum(n[k] / rates[k] for k in MUFU),
         "lsu": n["lds128"] / rates["lds128"],
         "issue": sum(n.values()) / LANES,
@@ -670,10 +685,7 @@ def run_ours(args, rank, world):
     dpt = shared_dpt(3, True)
     spb = shared_pipe_bound(rates, 3, True, dpt, active, sm_count)
     n = spb["ops_per_draw"]
-    # FP32 flops per draw-evaluation (FMA = 2): the d differences, the sum A
-    # and the sigmoid exponents (5d); where the sigmoid is evaluated, 1 + e,
-    # the running product, 1 - keep and the sum G (5d)
-    fp32_flops = 5 * 3 * (1.0 + active)
+    fp32_flops = shared_fp32_flops(3, True, active)
     fp32 = fp32_flops * rate
     fp32_peak = sm_count * LANES * 2 * SM_MAX_MHZ * 1e6
 
@@ -893,31 +905,37 @@ def paper_problem(pkg, ctx, n_alpha=2000, N1=10240, N2=20480):
             "paper_context": "mean 31.6 s per problem for the whole optimisation on a V100 (Sec. 3; 4.5 h / 513 problems)"}
 
 
-def c2_shared(pkg, ctx, c2):
-    """The d=3 grid's common-random-number groups (one stream per scenario)
-    evaluated by the shared-draw kernel, forward and forward + adjoint,
-    against the per-design kernel on the same seed (hits must agree)."""
+def shared_line(pkg, ctx, prob, d, rates, sm_count, h=0.01):
+    """A grid whose designs share one stream per scenario (common random
+    numbers) evaluated by the shared-draw kernel, forward and forward +
+    adjoint, against the per-design kernel on the same seed (hits must
+    agree); each with its min-over-pipes bound and FP32-pipe fraction."""
     import torch
-    dp = pkg.DeviceProblem.from_workload(c2)
-    jac = torch.as_tensor(c2.jac_packed(), dtype=torch.float64, device="cuda")
+    dp = pkg.DeviceProblem.from_workload(prob)
+    jac = torch.as_tensor(prob.jac_packed(), dtype=torch.float64, device="cuda")
     res = {}
     ref = pkg.Plan(ctx, dp)
     ref_hits = ref.eval(77)["hits"].clone()
     ref.close()
+    active = shared_active_fraction(prob, h, draws=256)
+    fp32_peak = sm_count * LANES * 2 * SM_MAX_MHZ * 1e6
     for grad in (False, True):
-        plan = pkg.Plan(ctx, dp, shared=True, grad=grad, k=4 if grad else 0)
-        run = (lambda s: plan.grad(s, jac, 0.01)) if grad else (lambda s: plan.eval(s))
+        plan = pkg.Plan(ctx, dp, shared=True, grad=grad, k=4 if grad else 0, timing=True)
+        run = (lambda s: plan.grad(s, jac, h)) if grad else (lambda s: plan.eval(s))
         run(76)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        ev[0].record()
         out = run(77)
-        ev[1].record()
-        ev[1].synchronize()
-        ms = ev[0].elapsed_time(ev[1])
+        ms = plan.kernel_ms()
         same = bool(torch.equal(out["hits"], ref_hits))
-        res["adj" if grad else "fwd"] = {"ms": ms, "draw_evals_per_s": c2.total_draws() / (ms / 1e3),
-                                         "hits_equal_per_design_kernel": same}
+        rate = prob.total_draws() / (ms / 1e3)
+        pb = shared_pipe_bound(rates, d, grad, shared_dpt(d, grad), active, sm_count)
+        res["adj" if grad else "fwd"] = {"kernel_ms": ms, "draw_evals_per_s": rate,
+                                         "hits_equal_per_design_kernel": same,
+                                         "pipe_bound": {"binding": pb["binding"], "bound": pb["bound_draw_evals_per_s"],
+                                                        "frac": rate / pb["bound_draw_evals_per_s"]},
+                                         "fp32_pipe_frac": rate * shared_fp32_flops(d, grad, active) / fp32_peak}
         plan.close()
+    res["adjoint_overhead"] = res["fwd"]["draw_evals_per_s"] / res["adj"]["draw_evals_per_s"]
+    res["active_fraction"] = active
     ctx.sync_status()
     return res
 
@@ -1052,8 +1070,12 @@ def run_extras(pkg, ctx, c2, rates, sm_count):
     ex["c3"] = c3_batched_vs_per_design(pkg, ctx)
     # d=10 gradient search (120 adjoint launches of 1e7 draws)
     ex["c4_search"] = c4_search(pkg, ctx)
-    # the d=3 grid by the shared-draw kernel (one stream per scenario)
-    ex["c2_shared"] = c2_shared(pkg, ctx, c2)
+    # the grids with one stream per scenario by the shared-draw kernel:
+    # d=3 (the step's grid), d=10 (AR(1), 1024 designs x 1e7) and d=20
+    # (block, 4096 designs x 1e7)
+    ex["c2_shared"] = shared_line(pkg, ctx, c2, 3, rates, sm_count)
+    ex["c4_shared"] = shared_line(pkg, ctx, c4, 10, rates, sm_count)
+    ex["c5_shared"] = shared_line(pkg, ctx, c5, 20, rates, sm_count)
     # one of the paper's optimisation problems at its own sizes (two-layer estimator)
     ex["paper_problem"] = paper_problem(pkg, ctx)
     # FWER constraint (Eq. 2) solved on the device for every split of the d=3 grid

@@ -82,6 +82,27 @@ __device__ __forceinline__ void make_batch(const float* __restrict__ sL, uint64_
     }
 }
 
+// Smallest of three floats in one instruction (three-input min).
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// The differences t_i - y_i, two coordinates per packed FMA: fma(y, -1, t)
+// rounds the exact t - y once, which is the FP32 subtraction bit for bit.
+template <int D>
+__device__ __forceinline__ void diffs(const float (&t)[D], const float* y, float (&dif)[D]) {
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+#pragma unroll
+    for (int i = 0; i + 1 < D; i += 2) {
+        const float2 r = __ffma2_rn(make_float2(y[i], y[i + 1]), m1, make_float2(t[i], t[i + 1]));
+        dif[i] = r.x;
+        dif[i + 1] = r.y;
+    }
+    if constexpr (D % 2 != 0) dif[D - 1] = __fsub_rn(t[D - 1], y[D - 1]);
+}
+
 template <int DP>
 __device__ __forceinline__ void load_row(const float* p, float* v) {
 #pragma unroll
@@ -95,10 +116,12 @@ __device__ __forceinline__ void load_row(const float* p, float* v) {
 // against this thread's first NQ designs.  y_i > t_i exactly when the FP32
 // difference t_i - y_i is negative: two unequal floats never subtract to
 // zero (gradual underflow), rounding keeps the sign, and the infinities
-// (dropped tests, draws outside the range) give +inf.  Forward: the hit is
-// the sign bit of the or of the differences (FADDs and one three-input or
-// per draw instead of a compare and a predicate merge per coordinate).
-// Adjoint: the hit is a negative smallest difference, and the same minimum
+// (dropped tests, draws outside the range) give +inf.  The differences go
+// two coordinates per packed FMA (diffs).  Forward: the hit is the sign bit
+// of the or of the differences (one three-input or per three coordinates
+// instead of a compare and a predicate merge per coordinate).  Adjoint: the
+// hit is a negative smallest difference (three-input minima), the sum A
+// over hits takes two coordinates per packed add, and the same minimum
 // gives the largest sigmoid exponent (below).  The draw loop is unrolled
 // (8 draws forward, 4 with the adjoint's larger bodies).
 template <int D, bool GRAD, int DPT, int NQ>
@@ -115,29 +138,33 @@ __device__ __forceinline__ void test_draws(const float* sy, const float* sz, int
         if constexpr (GRAD) load_row<DP>(sz + dn * DP, zz);
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
+            float dif[D];
+            diffs<D>(t[q], y, dif);
             if constexpr (!GRAD) {
                 uint32_t sgn = 0u;
 #pragma unroll
-                for (int i = 0; i < D; ++i) sgn |= __float_as_uint(__fsub_rn(t[q][i], y[i]));
+                for (int i = 0; i < D; ++i) sgn |= __float_as_uint(dif[i]);
                 cnt[q] += sgn >> 31;
             } else {
-                float dif[D], dmin = INFINITY;
+                float dmin = dif[0];
 #pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    dif[i] = __fsub_rn(t[q][i], y[i]);
-                    dmin = fminf(dmin, dif[i]);
-                }
+                for (int i = 1; i < D; i += 2) dmin = i + 1 < D ? fmin3(dmin, dif[i], dif[i + 1]) : fminf(dmin, dif[i]);
                 const bool hit = dmin < 0.0f;
                 cnt[q] += hit ? 1u : 0u;
                 // sum A over the hits (adding z, or nothing, as the FMA
                 // with a 0/1 factor does)
                 if (hit) {
 #pragma unroll
-                    for (int i = 0; i < D; ++i) A[q][i] = __fadd_rn(A[q][i], zz[i]);
+                    for (int i = 0; i + 1 < D; i += 2) {
+                        const float2 a = __fadd2_rn(make_float2(A[q][i], A[q][i + 1]), make_float2(zz[i], zz[i + 1]));
+                        A[q][i] = a.x;
+                        A[q][i + 1] = a.y;
+                    }
+                    if constexpr (D % 2 != 0) A[q][D - 1] = __fadd_rn(A[q][D - 1], zz[D - 1]);
                 }
                 if (nhl2e != 0.0f) {
                     // x_i = (y_i - t_i) log2(e) / h = (t_i - y_i) nhl2e, the
-                    // exponent of the sigmoid; the largest is dmin nhl2e
+                    // exponent of the sigmoid; the largest is xm = dmin nhl2e
                     // (nhl2e < 0, rounding is monotone).  When all x_i < -25
                     // the draw adds exactly zero to every G_i (2^x_i < 2^-25
                     // vanishes in 1 + 2^x_i, so every keep_i = 1).  When some
@@ -148,8 +175,10 @@ __device__ __forceinline__ void test_draws(const float* sy, const float* sz, int
                     // 6e-8 / h, far below its Monte Carlo error).  A warp
                     // takes the exponentials only when some lane's draw lies
                     // in [-25, 24).
-                    const float xm = dmin * nhl2e;
-                    if (__any_sync(0xffffffffu, xm >= -25.0f && xm < 24.0f)) {
+                    // xm + 1/2 in one FMA, so that the range [-25, 24)
+                    // is one comparison of its magnitude with 24.5
+                    const float xh = __fmaf_rn(dmin, nhl2e, 0.5f);
+                    if (__any_sync(0xffffffffu, fabsf(xh) < 24.5f)) {
                         float keep[D], prod = 1.0f;
 #pragma unroll
                         for (int i = 0; i < D; ++i) {
