@@ -50,12 +50,15 @@ __device__ __forceinline__ double fix_to_double(unsigned long long v) {
     return static_cast<double>(static_cast<long long>(v)) * (1.0 / static_cast<double>(1ull << kGradFixBits));
 }
 
-// Solve L^T g = v in place (L packed lower, FP64).
-__device__ __forceinline__ void solve_lt(const double* L, int d, double* v) {
+// Solve L^T g = v in place (L packed lower, FP64), with the reciprocals
+// rdiag[i] = 1 / L_ii computed once per design: FP64 division is a long
+// sequence on this GPU, and the batch-means error below takes a solve per
+// batch.
+__device__ __forceinline__ void solve_lt(const double* L, const double* rdiag, int d, double* v) {
     for (int i = d - 1; i >= 0; --i) {
         double s = v[i];
         for (int k = i + 1; k < d; ++k) s -= L[tri(k, i)] * v[k];
-        v[i] = s / L[tri(i, i)];
+        v[i] = s * rdiag[i];
     }
 }
 
@@ -83,6 +86,8 @@ __global__ void finalize_kernel(const FinalizeParams P, bool grad) {
     const double* J = P.jac ? P.jac + dr.vec_off * k : nullptr;
     if (k > 0 && !J) return;   // the host rejects this; never dereference a missing Jacobian
 
+    double rdiag[kMaxD];
+    for (int i = 0; i < d; ++i) rdiag[i] = 1.0 / L[tri(i, i)];
     double A[kMaxD], B[kMaxD], G[kMaxD];
     for (int i = 0; i < d; ++i) { A[i] = 0.0; B[i] = 0.0; G[i] = 0.0; }
     const unsigned long long* acc = P.gacc + dr.acc_off;
@@ -98,11 +103,12 @@ __global__ void finalize_kernel(const FinalizeParams P, bool grad) {
     }
     // likelihood ratio with the zero-mean control variate: L^-T (A - p B) / N
     double g[kMaxD], gs[kMaxD];
+    const double rN = N ? 1.0 / Nd : 0.0;
     for (int i = 0; i < d; ++i) {
-        g[i] = N ? (A[i] - p_any * B[i]) / Nd : 0.0;
-        gs[i] = (N && P.hinv > 0.0) ? G[i] * P.hinv / Nd : 0.0;
+        g[i] = (A[i] - p_any * B[i]) * rN;
+        gs[i] = P.hinv > 0.0 ? G[i] * P.hinv * rN : 0.0;
     }
-    solve_lt(L, d, g);
+    solve_lt(L, rdiag, d, g);
     double est[kMaxD], est_s[kMaxD];
     for (int m = 0; m < nout; ++m) {
         if (k > 0) {
@@ -121,13 +127,16 @@ __global__ void finalize_kernel(const FinalizeParams P, bool grad) {
     // batch means: per batch the same estimator on its own draws
     double ss[kMaxD];
     for (int m = 0; m < nout; ++m) ss[m] = 0.0;
+    uint64_t nb_last = 0;
+    double rnb = 0.0;                                 // 1 / nb, recomputed only when nb changes
     for (int bt = 0; bt < P.batches; ++bt) {
         const uint64_t nb = P.batch_draws[static_cast<int64_t>(j) * P.batches + bt];
         if (!nb) continue;
+        if (nb != nb_last) { rnb = 1.0 / static_cast<double>(nb); nb_last = nb; }
         const unsigned long long* a = acc + static_cast<int64_t>(bt) * 3 * d;
         double v[kMaxD];
-        for (int i = 0; i < d; ++i) v[i] = (fix_to_double(a[i]) - p_any * fix_to_double(a[d + i])) / static_cast<double>(nb);
-        solve_lt(L, d, v);
+        for (int i = 0; i < d; ++i) v[i] = (fix_to_double(a[i]) - p_any * fix_to_double(a[d + i])) * rnb;
+        solve_lt(L, rdiag, d, v);
         for (int m = 0; m < nout; ++m) {
             double c;
             if (k > 0) {
