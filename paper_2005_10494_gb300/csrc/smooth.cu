@@ -434,7 +434,10 @@ __device__ __forceinline__ void tile_outputs(float (*tile)[Tile2D<R>::SCP], int 
     const int orow = r0 + 4 * ty, ocol = c0 + 4 * tx;       // first output of this thread
     const int ncls = (R + 1) * (R + 1);
     typename GridWord<Elem>::W* O = out ? out + static_cast<int64_t>(s) * g1 * g2 : nullptr;
+    // the largest interior output of the patch and its position i * 4 + j
+    // (visited in row-major order, so a tie keeps the lowest index)
     float best = -INFINITY;
+    int bsel = -1;
     // Interior stencil of every output of the patch.  The interior window is
     // symmetric (tricube product weights, monomial basis), so its stencil
     // depends only on (|u|, |v|) sorted: (R+1)(R+2)/2 distinct weights, read
@@ -519,7 +522,10 @@ __device__ __forceinline__ void tile_outputs(float (*tile)[Tile2D<R>::SCP], int 
                 }
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) best = fmaxf(best, (row_int && col_int[j]) ? acc[i][j] : -INFINITY);
+            for (int j = 0; j < 4; ++j) {
+                const float v = (row_int && col_int[j]) ? acc[i][j] : -INFINITY;
+                if (v > best) { best = v; bsel = 4 * i + j; }
+            }
         }
     }
     // The tile's edge outputs (fewer than R rows or columns to a grid edge),
@@ -566,7 +572,15 @@ __device__ __forceinline__ void tile_outputs(float (*tile)[Tile2D<R>::SCP], int 
             if (a > eb_v || (a == eb_v && idx < eb_i)) { eb_v = a; eb_i = idx; }
         }
     }
-    best = fmaxf(best, eb_v);
+    // this thread's candidate: the interior best, or an edge output that is
+    // larger, or equal at a lower index
+    unsigned my_i = bsel >= 0 ? static_cast<unsigned>(orow + (bsel >> 2)) * static_cast<unsigned>(g2) +
+                                    static_cast<unsigned>(ocol + (bsel & 3))
+                              : 0xffffffffu;
+    if (eb_i >= 0 && (eb_v > best || (eb_v == best && static_cast<unsigned>(eb_i) < my_i))) {
+        best = eb_v;
+        my_i = static_cast<unsigned>(eb_i);
+    }
     // Argmax over the warp's outputs, without block barriers: the largest
     // value by max reductions, then the lowest index (within the grid,
     // below 2^31) holding it; one candidate per warp and tile, folded in
@@ -577,20 +591,7 @@ __device__ __forceinline__ void tile_outputs(float (*tile)[Tile2D<R>::SCP], int 
         float m = best;
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        unsigned cand = 0xffffffffu;
-        if (best == m && m > -INFINITY) {
-            if (eb_v == m) cand = static_cast<unsigned>(eb_i);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const bool row_int = orow + i >= R && orow + i <= g1 - 1 - R;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const bool v = row_int && ocol + j >= R && ocol + j <= g2 - 1 - R && acc[i][j] == m;
-                    const unsigned idx = static_cast<unsigned>(orow + i) * static_cast<unsigned>(g2) + static_cast<unsigned>(ocol + j);
-                    if (v && idx < cand) cand = idx;
-                }
-            }
-        }
+        const unsigned cand = (best == m && m > -INFINITY) ? my_i : 0xffffffffu;
         const unsigned wi = __reduce_min_sync(0xffffffffu, cand);
         if (lane == 0) {
             part_v[q] = wi != 0xffffffffu ? order_key(f2d_bits(m)) : 0ull;
