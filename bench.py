@@ -143,9 +143,11 @@ def shared_class_counts(d, grad, dpt, active=1.0):
     dpt designs.  Forward: the or of the d sign words with three-input logic
     (ceil((d-1)/2)) and the count add of the sign bit (ALU).  Adjoint: the
     smallest difference with three-input minima (ceil((d-1)/2)), the hit
-    test, the count (select and add), the range test of the largest sigmoid
-    exponent and the warp vote (ALU); the sum A over hits (floor(d/2) packed adds, one scalar for an
-    odd d) and the exponent (one FMA); the row of z; and, in the fraction
+    test, the count (select and add; at odd d none, see below), the range
+    test of the largest sigmoid exponent and the warp vote (ALU); the sum A
+    over hits (floor(d/2) packed adds; at odd d one more, whose second lane
+    counts the hit in the z row's padding slot) and the exponent (one FMA);
+    the row of z; and, in the fraction
     `active` of warp-draws where some lane's draw is within the sigmoid's
     reach, per coordinate the exponent, ex2, 1 + e, rcp, the running
     product, 1 - keep and the FMA of sum G (5d FP32, 2d MUFU)."""
@@ -154,9 +156,11 @@ def shared_class_counts(d, grad, dpt, active=1.0):
     c = {"mul_wide": 0.0, "alu": (d - 1 + 1) // 2 + 1.0, "ffma": float(odd), "ffma2": float(half),
          "lg2": 0.0, "sqrt": 0.0, "sin": 0.0, "cos": 0.0, "ex2": 0.0, "rcp": 0.0, "lds128": rows / float(dpt)}
     if grad:
-        c["alu"] = (d - 1 + 1) // 2 + 5.0
-        c["ffma2"] += half
-        c["ffma"] += odd + 1 + active * 5 * d
+        # at odd d the hit count rides in the last packed add of A (the z
+        # row's padding slot holds 1), instead of a select and an add
+        c["alu"] = (d - 1 + 1) // 2 + (3.0 if odd else 5.0)
+        c["ffma2"] += half + odd
+        c["ffma"] += 1 + active * 5 * d
         c["lds128"] += rows / float(dpt)
         c["ex2"] += active * d
         c["rcp"] += active * d

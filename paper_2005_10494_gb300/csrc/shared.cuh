@@ -34,6 +34,12 @@ struct SharedShape {
     // keep t (and the gradient sums) in registers
     static constexpr int kDpt = GRAD ? (D <= 4 ? 4 : (D <= 8 ? 2 : 1)) : (D <= 10 ? 4 : 2);
     static constexpr int kBD = kSharedThreads * Shape<D>::kG;        // draws per batch (one group per thread)
+    // adjoint at odd d: the z row carries 1 in its padding slot d for a
+    // valid draw, so the packed sum over hits, whose last pair would
+    // otherwise be a scalar add, counts them in A's slot d at no extra
+    // instruction; a tile has at most 2^18 draws, so the FP32 count is exact
+    static constexpr bool kCnt = GRAD && (D % 2 != 0);
+    static constexpr int kDA = D + (kCnt ? 1 : 0);                   // sums of A per design
     static constexpr size_t kSmem = static_cast<size_t>(kBD) * kDP * sizeof(float) * (GRAD ? 2 : 1);
 };
 
@@ -70,7 +76,10 @@ __device__ __forceinline__ void make_batch(const float* __restrict__ sL, uint64_
             if constexpr (GRAD) bsum[i] += zz[i];
         }
 #pragma unroll
-        for (int i = D; i < DP; ++i) { y[i] = -INFINITY; zz[i] = 0.0f; }
+        for (int i = D; i < DP; ++i) {
+            y[i] = -INFINITY;
+            zz[i] = (SharedShape<D, GRAD>::kCnt && i == D && valid) ? 1.0f : 0.0f;
+        }
         float4* yv = reinterpret_cast<float4*>(sy + (threadIdx.x * S::kG + g) * DP);
 #pragma unroll
         for (int v = 0; v < DP / 4; ++v) yv[v] = make_float4(y[4 * v], y[4 * v + 1], y[4 * v + 2], y[4 * v + 3]);
@@ -126,9 +135,11 @@ __device__ __forceinline__ void load_row(const float* p, float* v) {
 // (8 draws forward, 4 with the adjoint's larger bodies).
 template <int D, bool GRAD, int DPT, int NQ>
 __device__ __forceinline__ void test_draws(const float* sy, const float* sz, int nb, const float (&t)[DPT][D],
-                                           float nhl2e, uint32_t (&cnt)[DPT], float (&A)[DPT][GRAD ? D : 1],
+                                           float nhl2e, uint32_t (&cnt)[DPT],
+                                           float (&A)[DPT][GRAD ? SharedShape<D, GRAD>::kDA : 1],
                                            float (&G)[DPT][GRAD ? D : 1]) {
     constexpr int DP = SharedShape<D, GRAD>::kDP;
+    constexpr int DA = SharedShape<D, GRAD>::kDA;
     constexpr int kUnroll = GRAD ? 4 : 8;
 #pragma unroll kUnroll
     for (int dn = 0; dn < nb; ++dn) {
@@ -150,17 +161,17 @@ __device__ __forceinline__ void test_draws(const float* sy, const float* sz, int
 #pragma unroll
                 for (int i = 1; i < D; i += 2) dmin = i + 1 < D ? fmin3(dmin, dif[i], dif[i + 1]) : fminf(dmin, dif[i]);
                 const bool hit = dmin < 0.0f;
-                cnt[q] += hit ? 1u : 0u;
+                if constexpr (!SharedShape<D, GRAD>::kCnt) cnt[q] += hit ? 1u : 0u;
                 // sum A over the hits (adding z, or nothing, as the FMA
-                // with a 0/1 factor does)
+                // with a 0/1 factor does), and the count in slot d
                 if (hit) {
 #pragma unroll
-                    for (int i = 0; i + 1 < D; i += 2) {
+                    for (int i = 0; i + 1 < DA; i += 2) {
                         const float2 a = __fadd2_rn(make_float2(A[q][i], A[q][i + 1]), make_float2(zz[i], zz[i + 1]));
                         A[q][i] = a.x;
                         A[q][i + 1] = a.y;
                     }
-                    if constexpr (D % 2 != 0) A[q][D - 1] = __fadd_rn(A[q][D - 1], zz[D - 1]);
+                    if constexpr (DA % 2 != 0) A[q][DA - 1] = __fadd_rn(A[q][DA - 1], zz[DA - 1]);
                 }
                 if (nhl2e != 0.0f) {
                     // x_i = (y_i - t_i) log2(e) / h = (t_i - y_i) nhl2e, the
@@ -250,12 +261,14 @@ __device__ __forceinline__ void shared_body(const SampleParams& P, const SharedT
         const Round1 r1 = round1_consts(static_cast<uint32_t>(call_first >> 32), tl.key, P.rk0, P.rk1);
 
         uint32_t cnt[DPT];
-        float A[DPT][GRAD ? D : 1], G[DPT][GRAD ? D : 1], bsum[GRAD ? D : 1];
+        float A[DPT][GRAD ? SS::kDA : 1], G[DPT][GRAD ? D : 1], bsum[GRAD ? D : 1];
 #pragma unroll
         for (int q = 0; q < DPT; ++q) {
             cnt[q] = 0;
 #pragma unroll
-            for (int i = 0; i < (GRAD ? D : 1); ++i) { A[q][i] = 0.0f; G[q][i] = 0.0f; }
+            for (int i = 0; i < (GRAD ? SS::kDA : 1); ++i) A[q][i] = 0.0f;
+#pragma unroll
+            for (int i = 0; i < (GRAD ? D : 1); ++i) G[q][i] = 0.0f;
         }
 #pragma unroll
         for (int i = 0; i < (GRAD ? D : 1); ++i) bsum[i] = 0.0f;
@@ -282,6 +295,10 @@ __device__ __forceinline__ void shared_body(const SampleParams& P, const SharedT
         }
 
         // hits: each design of the tile belongs to exactly one thread
+        if constexpr (SS::kCnt) {
+#pragma unroll
+            for (int q = 0; q < DPT; ++q) cnt[q] = static_cast<uint32_t>(A[q][D]);
+        }
 #pragma unroll
         for (int q = 0; q < DPT; ++q)
             if (dsg[q] >= 0 && cnt[q]) atomicAdd(&P.hits[dsg[q]], static_cast<unsigned long long>(cnt[q]));
