@@ -156,3 +156,17 @@ def test_gradient_se_is_calibrated_across_seeds(ctx, shared):
     ok = emp > 0
     ratio = float(np.median(rep[ok] / emp[ok]))
     assert 0.85 < ratio < 1.15, ratio
+
+
+@pytest.mark.parametrize("d_list", [(1, 2, 3, 4), (5, 6, 7, 8), (9, 11, 12, 13), (14, 15, 16, 17), (18, 19, 20)])
+def test_shared_adjoint_hits_identical_to_per_design(ctx, d_list):
+    """The adjoint form of the shared-draw kernel counts its hits in the
+    padded slot of the sum A when d is not a multiple of 4 (and by integer
+    adds otherwise): the counts equal the per-design kernel's at every d."""
+    prob = workloads.crn_groups(np.random.default_rng(50 + sum(d_list)), d_list=d_list, group=36, extra=2,
+                                n_draws=30_011, draw_begin=3)
+    per = run(ctx, prob, seed=8, grad=True, h=0.02)
+    sh = run(ctx, prob, seed=8, grad=True, h=0.02, shared=True)
+    np.testing.assert_array_equal(sh["hits"], per["hits"])
+    np.testing.assert_array_equal(sh["p"], per["p"])
+    _grad_close(sh, per)
