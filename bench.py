@@ -143,14 +143,15 @@ def shared_class_counts(d, grad, dpt, active=1.0):
     dpt designs.  Forward: the or of the d sign words with three-input logic
     (ceil((d-1)/2)) and the count add of the sign bit (ALU).  Adjoint: the
     smallest difference with three-input minima (ceil((d-1)/2)), the hit
-    test, the count (select and add; at odd d none, see below), the range
-    test of the largest sigmoid exponent and the warp vote (ALU); the sum A
-    over hits (floor(d/2) packed adds; at odd d one more, whose second lane
-    counts the hit in the z row's padding slot) and the exponent (one FMA);
-    the row of z; and, in the fraction
-    `active` of warp-draws where some lane's draw is within the sigmoid's
-    reach, per coordinate the exponent, ex2, 1 + e, rcp, the running
-    product, 1 - keep and the FMA of sum G (5d FP32, 2d MUFU)."""
+    test, the count (select and add; at odd d none, see below), the window
+    test |min_i (t_i - y_i)| < w of the sigmoid's reach (one compare of a
+    magnitude) and the warp vote (ALU); the sum A over hits (floor(d/2)
+    packed adds; at odd d one more, whose second lane counts the hit in the
+    z row's padding slot); the row of z; and, in the fraction `active` of
+    warp-draws where some lane's draw is within that window, per coordinate
+    the exponent, 1 + e, 1 - keep and the FMA of sum G two coordinates per
+    packed instruction (4 floor(d/2) `ffma2`, 4 scalar at odd d), the
+    running product (d scalar), ex2 and rcp (2d MUFU)."""
     rows = -(-d // 4)
     half, odd = d // 2, d % 2
     c = {"mul_wide": 0.0, "alu": (d - 1 + 1) // 2 + 1.0, "ffma": float(odd), "ffma2": float(half),
@@ -160,7 +161,8 @@ def shared_class_counts(d, grad, dpt, active=1.0):
         # row's padding slot holds 1), instead of a select and an add
         c["alu"] = (d - 1 + 1) // 2 + (3.0 if odd else 5.0)
         c["ffma2"] += half + odd
-        c["ffma"] += 1 + active * 5 * d
+        c["ffma"] += active * (d + 4 * odd)
+        c["ffma2"] += active * 4 * half
         c["lds128"] += rows / float(dpt)
         c["ex2"] += active * d
         c["rcp"] += active * d
@@ -169,21 +171,21 @@ def shared_class_counts(d, grad, dpt, active=1.0):
 
 def shared_fp32_flops(d, grad, active=1.0):
     """Algorithmic FP32 flops per draw-evaluation of the shared-draw kernel
-    (FMA = 2): d differences; the adjoint adds the d sums of A, the exponent
-    FMA and, where the sigmoid is taken, per coordinate its exponent, 1 + e,
-    the product, 1 - keep and the FMA of G (6d)."""
+    (FMA = 2): d differences; the adjoint adds the d sums of A and, where the
+    sigmoid is taken, per coordinate its exponent, 1 + e, the product,
+    1 - keep and the FMA of G (6d)."""
     f = float(d)
     if grad:
-        f += d + 2 + 6 * d * active
+        f += d + 6 * d * active
     return f
 
 
 def shared_active_fraction(prob, h, draws=1024, warp=32, seed=0):
     """Fraction of (32-design block, draw) pairs of the shared-draw kernel in
     which some design's draw has a sigmoid exponent x_max = max_i (y_i - t_i)
-    log2(e) / h in [-25, 24), i.e. where the kernel evaluates the smoothed
-    indicator (elsewhere every contribution is zero or below 6e-8 and the
-    kernel skips it).  A warp tests 32
+    log2(e) / h with |x_max| < 25.03, i.e. where the kernel evaluates the
+    smoothed indicator (elsewhere every contribution is zero or below 3e-8
+    and the kernel skips it).  A warp tests 32
     consecutive designs of a group against one draw; estimated on `draws`
     normal draws per scenario (numpy FP64, not the kernel's stream: this is
     a property of the workload)."""
@@ -199,7 +201,7 @@ def shared_active_fraction(prob, h, draws=1024, warp=32, seed=0):
         t = np.stack([prob.t(j) for j in idx])
         for w0 in range(0, idx.size, warp):
             xm = ((y[:, None, :] - t[None, w0:w0 + warp, :]) * l2e).max(axis=2)
-            a = ((xm >= -25.0) & (xm < 24.0)).any(axis=1)
+            a = (np.abs(xm) < 25.03).any(axis=1)
             act += int(a.sum())
             tot += a.size
     return act / max(tot, 1)

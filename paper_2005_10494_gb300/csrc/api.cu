@@ -619,6 +619,7 @@ mcd_status enqueue(mcd_plan* pl, const LaunchArgs& a, cudaStream_t stream) {
         sp.gacc = pl->d_gacc;
         sp.batches = pl->batches;
         sp.hinv_log2e = (a.grad && a.h > 0.0) ? static_cast<float>(1.4426950408889634 / a.h) : 0.0f;
+        sp.sig_skip_w = (a.grad && a.h > 0.0) ? static_cast<float>(25.03 * a.h / 1.4426950408889634) : -1.0f;
         sp.hinv = (a.grad && a.h > 0.0) ? 1.0 / a.h : 0.0;
         sp.status = ctx->d_status;
         fill_round_keys(a.seed, sp);

@@ -75,6 +75,7 @@ struct SampleParams {
     unsigned long long* gacc;       // fixed-point gradient accumulators (grad launches)
     int32_t          batches;       // batch-means slots per design
     float            hinv_log2e;    // log2(e) / h for the smoothed indicator (0: off)
+    float            sig_skip_w;    // 25.03 h / log2(e): shared-draw sigmoid window half-width (-1: off)
     double           hinv;          // 1 / h (FP64 path)
     uint32_t         rk0[10];       // Philox round keys (seed_lo + r W0)
     uint32_t         rk1[10];       // Philox round keys (seed_hi + r W1)

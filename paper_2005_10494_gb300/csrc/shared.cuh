@@ -135,7 +135,7 @@ __device__ __forceinline__ void load_row(const float* p, float* v) {
 // (8 draws forward, 4 with the adjoint's larger bodies).
 template <int D, bool GRAD, int DPT, int NQ>
 __device__ __forceinline__ void test_draws(const float* sy, const float* sz, int nb, const float (&t)[DPT][D],
-                                           float nhl2e, uint32_t (&cnt)[DPT],
+                                           float nhl2e, float wsk, uint32_t (&cnt)[DPT],
                                            float (&A)[DPT][GRAD ? SharedShape<D, GRAD>::kDA : 1],
                                            float (&G)[DPT][GRAD ? D : 1]) {
     constexpr int DP = SharedShape<D, GRAD>::kDP;
@@ -173,31 +173,44 @@ __device__ __forceinline__ void test_draws(const float* sy, const float* sz, int
                     }
                     if constexpr (DA % 2 != 0) A[q][DA - 1] = __fadd_rn(A[q][DA - 1], zz[DA - 1]);
                 }
-                if (nhl2e != 0.0f) {
+                {
                     // x_i = (y_i - t_i) log2(e) / h = (t_i - y_i) nhl2e, the
                     // exponent of the sigmoid; the largest is xm = dmin nhl2e
-                    // (nhl2e < 0, rounding is monotone).  When all x_i < -25
-                    // the draw adds exactly zero to every G_i (2^x_i < 2^-25
-                    // vanishes in 1 + 2^x_i, so every keep_i = 1).  When some
-                    // x_k >= 24, keep_k = 1 / (1 + 2^x_k) < 2^-24 bounds the
-                    // product, so every contribution prod (1 - keep_i) is
-                    // below 6e-8: such draws are skipped too, which moves
-                    // G / N by less than 6e-8 (the derivative by less than
-                    // 6e-8 / h, far below its Monte Carlo error).  A warp
-                    // takes the exponentials only when some lane's draw lies
-                    // in [-25, 24).
-                    // xm + 1/2 in one FMA, so that the range [-25, 24)
-                    // is one comparison of its magnitude with 24.5
-                    const float xh = __fmaf_rn(dmin, nhl2e, 0.5f);
-                    if (__any_sync(0xffffffffu, fabsf(xh) < 24.5f)) {
+                    // (nhl2e < 0).  wsk = 25.03 / |nhl2e| (to FP32 rounding), so |dmin| >= wsk
+                    // gives |xm| > 25.02 after rounding.  When xm < -25 (dmin
+                    // >= wsk) every x_i < -25 and the draw adds exactly zero
+                    // to every G_i (2^x_i < 2^-25 vanishes in 1 + 2^x_i, so
+                    // every keep_i = 1).  When xm > 25 (dmin <= -wsk), keep_k
+                    // = 1 / (1 + 2^xm) < 2^-25 bounds the product, so every
+                    // contribution prod (1 - keep_i) is below 3e-8: such
+                    // draws are skipped too, which moves G / N by less than
+                    // 3e-8 (the derivative by less than 3e-8 / h, far below
+                    // its Monte Carlo error).  A warp takes the exponentials
+                    // only when some lane's draw has |dmin| < wsk: one
+                    // comparison of a magnitude.  wsk < 0 (no sigmoid sums)
+                    // never passes.
+                    if (__any_sync(0xffffffffu, fabsf(dmin) < wsk)) {
                         float keep[D], prod = 1.0f;
+                        const float2 nh2 = make_float2(nhl2e, nhl2e), one2 = make_float2(1.0f, 1.0f);
 #pragma unroll
-                        for (int i = 0; i < D; ++i) {
-                            keep[i] = rcp_approx(1.0f + ex2_approx(dif[i] * nhl2e));
-                            prod *= keep[i];
+                        for (int i = 0; i + 1 < D; i += 2) {
+                            const float2 x = __fmul2_rn(make_float2(dif[i], dif[i + 1]), nh2);
+                            const float2 u = __fadd2_rn(one2, make_float2(ex2_approx(x.x), ex2_approx(x.y)));
+                            keep[i] = rcp_approx(u.x);
+                            keep[i + 1] = rcp_approx(u.y);
                         }
+                        if constexpr (D % 2 != 0) keep[D - 1] = rcp_approx(1.0f + ex2_approx(dif[D - 1] * nhl2e));
 #pragma unroll
-                        for (int i = 0; i < D; ++i) G[q][i] = fmadd(prod, 1.0f - keep[i], G[q][i]);
+                        for (int i = 0; i < D; ++i) prod *= keep[i];
+                        const float2 pr2 = make_float2(prod, prod), m1 = make_float2(-1.0f, -1.0f);
+#pragma unroll
+                        for (int i = 0; i + 1 < D; i += 2) {
+                            const float2 omk = __ffma2_rn(make_float2(keep[i], keep[i + 1]), m1, one2);
+                            const float2 g = __ffma2_rn(pr2, omk, make_float2(G[q][i], G[q][i + 1]));
+                            G[q][i] = g.x;
+                            G[q][i + 1] = g.y;
+                        }
+                        if constexpr (D % 2 != 0) G[q][D - 1] = fmadd(prod, 1.0f - keep[D - 1], G[q][D - 1]);
                     }
                 }
             }
@@ -258,6 +271,11 @@ __device__ __forceinline__ void shared_body(const SampleParams& P, const SharedT
         const uint64_t call_first = g_first * static_cast<uint64_t>(S::kNC);
         const uint64_t call_last = (g_first + ngroups) * static_cast<uint64_t>(S::kNC) - 1;
         const bool fast = (call_first >> 32) == (call_last >> 32);
+        // the sigmoid's exponent scale -log2(e)/h, and the half-width
+        // 25.03 h / log2(e) of the window of differences in which its work
+        // is taken (test_draws; -1 when the sigmoid sums are off)
+        const float nhl2e = GRAD ? -P.hinv_log2e : 0.0f;
+        const float wsk = GRAD ? P.sig_skip_w : -1.0f;
         const Round1 r1 = round1_consts(static_cast<uint32_t>(call_first >> 32), tl.key, P.rk0, P.rk1);
 
         uint32_t cnt[DPT];
@@ -272,7 +290,6 @@ __device__ __forceinline__ void shared_body(const SampleParams& P, const SharedT
         }
 #pragma unroll
         for (int i = 0; i < (GRAD ? D : 1); ++i) bsum[i] = 0.0f;
-        const float nhl2e = GRAD ? -P.hinv_log2e : 0.0f;
 
         for (uint32_t g0 = 0; g0 < ngroups; g0 += blockDim.x) {
             const uint32_t gi = g0 + threadIdx.x;
@@ -283,12 +300,12 @@ __device__ __forceinline__ void shared_body(const SampleParams& P, const SharedT
             const int nb = static_cast<int>(min(static_cast<uint32_t>(SS::kBD), (ngroups - g0) * S::kG));
             // nq is block-uniform: one branch per batch picks the loop for
             // exactly nq designs per thread
-            if (nq >= DPT) test_draws<D, GRAD, DPT, DPT>(sy, sz, nb, t, nhl2e, cnt, A, G);
+            if (nq >= DPT) test_draws<D, GRAD, DPT, DPT>(sy, sz, nb, t, nhl2e, wsk, cnt, A, G);
             else if constexpr (DPT > 1) {
-                if (nq == 1) test_draws<D, GRAD, DPT, 1>(sy, sz, nb, t, nhl2e, cnt, A, G);
+                if (nq == 1) test_draws<D, GRAD, DPT, 1>(sy, sz, nb, t, nhl2e, wsk, cnt, A, G);
                 else if constexpr (DPT > 2) {
-                    if (nq == 2) test_draws<D, GRAD, DPT, 2>(sy, sz, nb, t, nhl2e, cnt, A, G);
-                    else if constexpr (DPT > 3) test_draws<D, GRAD, DPT, 3>(sy, sz, nb, t, nhl2e, cnt, A, G);
+                    if (nq == 2) test_draws<D, GRAD, DPT, 2>(sy, sz, nb, t, nhl2e, wsk, cnt, A, G);
+                    else if constexpr (DPT > 3) test_draws<D, GRAD, DPT, 3>(sy, sz, nb, t, nhl2e, wsk, cnt, A, G);
                 }
             }
             __syncthreads();                          // the next batch rewrites sy / sz

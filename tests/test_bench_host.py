@@ -112,19 +112,22 @@ def test_shared_class_counts_and_bound():
     assert f["ffma2"] == 1 and f["ffma"] == 1 and f["alu"] == 2 and f["lds128"] == pytest.approx(0.25)
     assert f["ex2"] == f["rcp"] == f["mul_wide"] == 0
     g = bench.shared_class_counts(3, True, 4, active=0.5)
-    assert g["ffma2"] == 3 and g["alu"] == 4
+    # packed: 1 difference pair + 2 sum pairs, and 4 pairs of sigmoid work
+    # in half the warp-draws; scalar: the odd difference, and the odd
+    # coordinate's 4 plus the 3 products of the running product
+    assert g["ffma2"] == pytest.approx(3 + 0.5 * 4) and g["alu"] == 4
     assert g["ex2"] == g["rcp"] == pytest.approx(1.5)
-    assert g["ffma"] == pytest.approx(2 + 0.5 * 15)
+    assert g["ffma"] == pytest.approx(1 + 0.5 * 7)
     assert g["lds128"] == pytest.approx(0.5)
     e = bench.shared_class_counts(10, True, 1, active=0.0)
-    assert e["ffma2"] == 10 and e["ffma"] == 1 and e["alu"] == 5 + 5
+    assert e["ffma2"] == 10 and e["ffma"] == 0 and e["alu"] == 5 + 5
     o = bench.shared_class_counts(5, True, 2, active=0.0)
-    assert o["ffma2"] == 2 + 3 and o["ffma"] == 2 and o["alu"] == 2 + 3
+    assert o["ffma2"] == 2 + 3 and o["ffma"] == 1 and o["alu"] == 2 + 3
     rates = {"lop3": 64.0, "ffma": 128.0, "ffma2": 64.0, "lg2": 16.0, "sqrt": 16.0, "sin": 16.0, "cos": 16.0,
              "ex2": 32.0, "rcp": 16.0, "lds128": 16.0}
     b = bench.shared_pipe_bound(rates, 3, True, 4, 1.0, 152, mhz=2000.0)
     assert b["sm_clk_per_draw"]["mufu"] == pytest.approx(3 / 32 + 3 / 16)
-    assert b["sm_clk_per_draw"]["fp32"] == pytest.approx((2 + 15) / 128 + 3 / 64)
+    assert b["sm_clk_per_draw"]["fp32"] == pytest.approx((1 + 7) / 128 + (3 + 4) / 64)
     full = bench.shared_class_counts(3, True, 4, active=1.0)
     assert b["sm_clk_per_draw"]["issue"] == pytest.approx(sum(full.values()) / 128)
     slow = dict(rates, ex2=4.0, rcp=4.0)
@@ -134,7 +137,7 @@ def test_shared_class_counts_and_bound():
     assert b0["sm_clk_per_draw"]["alu"] == pytest.approx(4 / 64.0)
     assert b0["bound_draw_evals_per_s"] > b["bound_draw_evals_per_s"]
     assert bench.shared_fp32_flops(3, False) == 3
-    assert bench.shared_fp32_flops(3, True, 0.5) == pytest.approx(3 + 3 + 2 + 9)
+    assert bench.shared_fp32_flops(3, True, 0.5) == pytest.approx(3 + 3 + 9)
 
 
 def test_shared_active_fraction_limits():
