@@ -40,6 +40,26 @@ struct SharedShape {
     // instruction; a tile has at most 2^18 draws, so the FP32 count is exact
     static constexpr bool kCnt = GRAD && (D % 2 != 0);
     static constexpr int kDA = D + (kCnt ? 1 : 0);                   // sums of A per design
+    // Register layout per d, chosen by timing each d on d-dimensional
+    // common-random-number grids (2048 designs x 2e6 draws), forward and
+    // adjoint, against the plain layout (G in registers, draw loop unrolled
+    // 4 / 8 times, normals of a group made up front, no register bound):
+    // - kWide (adjoint at d = 11, 14, 16, 18, 20): the sigmoid sums G in
+    //   thread-private shared memory (touched only in the warp-draws that
+    //   reach the sigmoid), the draw loop unrolled twice and the kernel held
+    //   to 128 registers: two blocks per SM instead of one, 5-21 % faster;
+    static constexpr bool kWide = GRAD && (D == 11 || D == 14 || D == 16 || D == 18 || D == 20);
+    static constexpr int kUnroll = GRAD ? (kWide ? 2 : 4) : 8;
+    // - kBound2: 128 registers (two blocks per SM) for kWide, and for the
+    //   forward kernel at d >= 9 except 10 and 12 (which fit two blocks
+    //   anyway): 2-13 % faster;
+    static constexpr bool kBound2 = kWide || (!GRAD && D >= 9 && D != 10 && D != 12);
+    // - kProg (odd d >= 9): each draw's normals made just before its
+    //   transform (make_batch); a group holds four draws at odd d, whose
+    //   4 d normals made up front need as many registers.  It lets the
+    //   d = 9 adjoint fit two blocks per SM unbounded (28 % faster) and the
+    //   bounded kernels above spill less.
+    static constexpr bool kProg = D >= 9 && D % 2 != 0;
     static constexpr size_t kSmem = static_cast<size_t>(kBD) * kDP * sizeof(float) * (GRAD ? 2 : 1);
 };
 
@@ -53,16 +73,32 @@ __device__ __forceinline__ void make_batch(const float* __restrict__ sL, uint64_
                                            float* bsum) {
     using S = Shape<D>;
     constexpr int DP = SharedShape<D, GRAD>::kDP;
+    constexpr bool kProg = SharedShape<D, GRAD>::kProg;
     float z[S::kNZ];
+    if constexpr (!kProg) {
 #pragma unroll
-    for (int c = 0; c < S::kNC; ++c) {
-        uint4 w;
-        if (fast) w = philox_fast(call_lo + c, r1, P.rk0, P.rk1);
-        else w = philox_full(call + c, key, P.rk0, P.rk1);
-        normals4<float>(w, &z[4 * c]);
+        for (int c = 0; c < S::kNC; ++c) {
+            uint4 w;
+            if (fast) w = philox_fast(call_lo + c, r1, P.rk0, P.rk1);
+            else w = philox_full(call + c, key, P.rk0, P.rk1);
+            normals4<float>(w, &z[4 * c]);
+        }
     }
 #pragma unroll
     for (int g = 0; g < S::kG; ++g) {
+        if constexpr (kProg) {
+            // the Philox calls whose normals draw g is the first to use
+            // (draw g takes normals g d .. g d + d - 1, four per call), made
+            // just before its transform so that the normals of earlier draws
+            // are dead by then
+#pragma unroll
+            for (int c = (g * D + 3) / 4; c < ((g + 1) * D + 3) / 4; ++c) {
+                uint4 w;
+                if (fast) w = philox_fast(call_lo + c, r1, P.rk0, P.rk1);
+                else w = philox_full(call + c, key, P.rk0, P.rk1);
+                normals4<float>(w, &z[4 * c]);
+            }
+        }
         const bool valid = (base + g - ofs) < n;
         float y[DP], zz[DP];
 #pragma unroll
@@ -90,6 +126,19 @@ __device__ __forceinline__ void make_batch(const float* __restrict__ sL, uint64_
         }
     }
 }
+
+// The sigmoid sums G of a thread's DPT designs: registers, or (SH)
+// thread-private shared-memory slots strided by the block size (`s` points
+// at the thread's first slot), so that a warp's accesses hit 32 banks.
+template <int D, int DPT, bool SH>
+struct GSums {
+    float r[SH ? 1 : DPT][SH ? 1 : D];
+    float* s;
+    __device__ __forceinline__ float& operator()(int q, int i) {
+        if constexpr (SH) return s[(q * D + i) * kSharedThreads];
+        else return r[q][i];
+    }
+};
 
 // Smallest of three floats in one instruction (three-input min).
 __device__ __forceinline__ float fmin3(float a, float b, float c) {
@@ -137,10 +186,10 @@ template <int D, bool GRAD, int DPT, int NQ>
 __device__ __forceinline__ void test_draws(const float* sy, const float* sz, int nb, const float (&t)[DPT][D],
                                            float nhl2e, float wsk, uint32_t (&cnt)[DPT],
                                            float (&A)[DPT][GRAD ? SharedShape<D, GRAD>::kDA : 1],
-                                           float (&G)[DPT][GRAD ? D : 1]) {
+                                           GSums<D, DPT, SharedShape<D, GRAD>::kWide>& G) {
     constexpr int DP = SharedShape<D, GRAD>::kDP;
     constexpr int DA = SharedShape<D, GRAD>::kDA;
-    constexpr int kUnroll = GRAD ? 4 : 8;
+    constexpr int kUnroll = SharedShape<D, GRAD>::kUnroll;
 #pragma unroll kUnroll
     for (int dn = 0; dn < nb; ++dn) {
         float y[DP];
@@ -206,11 +255,11 @@ __device__ __forceinline__ void test_draws(const float* sy, const float* sz, int
 #pragma unroll
                         for (int i = 0; i + 1 < D; i += 2) {
                             const float2 omk = __ffma2_rn(make_float2(keep[i], keep[i + 1]), m1, one2);
-                            const float2 g = __ffma2_rn(pr2, omk, make_float2(G[q][i], G[q][i + 1]));
-                            G[q][i] = g.x;
-                            G[q][i + 1] = g.y;
+                            const float2 g = __ffma2_rn(pr2, omk, make_float2(G(q, i), G(q, i + 1)));
+                            G(q, i) = g.x;
+                            G(q, i + 1) = g.y;
                         }
-                        if constexpr (D % 2 != 0) G[q][D - 1] = fmadd(prod, 1.0f - keep[D - 1], G[q][D - 1]);
+                        if constexpr (D % 2 != 0) G(q, D - 1) = fmadd(prod, 1.0f - keep[D - 1], G(q, D - 1));
                     }
                 }
             }
@@ -231,6 +280,7 @@ __device__ __forceinline__ void shared_body(const SampleParams& P, const SharedT
     __shared__ __align__(16) float sL[LPad<float>::rowoff(D) + 4];
     __shared__ float sB[kMaxWarps][GRAD ? D : 1];
     __shared__ unsigned int s_tile;
+    __shared__ float sGw[SS::kWide ? kSharedThreads * DPT * D : 1];   // G slots (kWide)
 
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(P.ticket, 1u);
@@ -279,14 +329,17 @@ __device__ __forceinline__ void shared_body(const SampleParams& P, const SharedT
         const Round1 r1 = round1_consts(static_cast<uint32_t>(call_first >> 32), tl.key, P.rk0, P.rk1);
 
         uint32_t cnt[DPT];
-        float A[DPT][GRAD ? SS::kDA : 1], G[DPT][GRAD ? D : 1], bsum[GRAD ? D : 1];
+        float A[DPT][GRAD ? SS::kDA : 1], bsum[GRAD ? D : 1];
+        GSums<D, DPT, SS::kWide> G;
+        G.s = sGw + threadIdx.x;
 #pragma unroll
         for (int q = 0; q < DPT; ++q) {
             cnt[q] = 0;
 #pragma unroll
             for (int i = 0; i < (GRAD ? SS::kDA : 1); ++i) A[q][i] = 0.0f;
 #pragma unroll
-            for (int i = 0; i < (GRAD ? D : 1); ++i) G[q][i] = 0.0f;
+            for (int i = 0; i < D; ++i)
+                if constexpr (GRAD) G(q, i) = 0.0f;
         }
 #pragma unroll
         for (int i = 0; i < (GRAD ? D : 1); ++i) bsum[i] = 0.0f;
@@ -339,7 +392,7 @@ __device__ __forceinline__ void shared_body(const SampleParams& P, const SharedT
                     for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) s += static_cast<double>(sB[w][i]);
                     atomicAdd(slot + i, static_cast<unsigned long long>(__double2ll_rn(static_cast<double>(A[q][i]) * fix)));
                     atomicAdd(slot + D + i, static_cast<unsigned long long>(__double2ll_rn(s * fix)));
-                    atomicAdd(slot + 2 * D + i, static_cast<unsigned long long>(__double2ll_rn(static_cast<double>(G[q][i]) * fix)));
+                    atomicAdd(slot + 2 * D + i, static_cast<unsigned long long>(__double2ll_rn(static_cast<double>(G(q, i)) * fix)));
                 }
             }
         }
@@ -366,9 +419,19 @@ __global__ void __launch_bounds__(kSharedThreads, 3) shared_kernel_3b(const __gr
     shared_body<D, GRAD>(P, tiles, list);
 }
 
+// Two resident blocks per SM (at most 128 registers a thread), at the
+// dimensions SharedShape::kBound2 lists.
+template <int D, bool GRAD>
+__global__ void __launch_bounds__(kSharedThreads, 2) shared_kernel_2b(const __grid_constant__ SampleParams P,
+                                                                      const SharedTile* __restrict__ tiles,
+                                                                      const uint32_t* __restrict__ list) {
+    shared_body<D, GRAD>(P, tiles, list);
+}
+
 template <int D, bool GRAD>
 const void* shared_fn() {
     if constexpr (GRAD && D <= 3) return reinterpret_cast<const void*>(&shared_kernel_3b<D, GRAD>);
+    else if constexpr (SharedShape<D, GRAD>::kBound2) return reinterpret_cast<const void*>(&shared_kernel_2b<D, GRAD>);
     else return reinterpret_cast<const void*>(&shared_kernel<D, GRAD>);
 }
 
