@@ -215,8 +215,7 @@ mcd_status mc_design_grad(mcd_ctx* ctx, const mcd_problem* prob, uint64_t seed,
  *   calls whose GPU work overlaps -- on different streams, or from several
  *   host threads -- race on it and must be serialised by the caller.
  *   Set-up: the first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture.
+ *   (cudaGetSymbolAddress) with that device current.
  *   Limits: n_scen == 1, n_design <= 16384, every n_draws[j] equal,
  *   draw_begin NULL or all 0; otherwise MCD_EINVAL, before any work.
  *   Inputs and outputs as in mc_design_eval (the stream keys are copied from
