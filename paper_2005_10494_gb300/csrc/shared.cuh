@@ -180,8 +180,9 @@ __device__ __forceinline__ void load_row(const float* p, float* v) {
 // instead of a compare and a predicate merge per coordinate).  Adjoint: the
 // hit is a negative smallest difference (three-input minima), the sum A
 // over hits takes two coordinates per packed add, and the same minimum
-// gives the largest sigmoid exponent (below).  The draw loop is unrolled
-// (8 draws forward, 4 with the adjoint's larger bodies).
+// gives the largest sigmoid exponent (below); the minimum is formed one
+// design ahead.  The draw loop is unrolled (8 draws forward, 4 or 2 with
+// the adjoint's larger bodies, SharedShape::kUnroll).
 template <int D, bool GRAD, int DPT, int NQ>
 __device__ __forceinline__ void test_draws(const float* sy, const float* sz, int nb, const float (&t)[DPT][D],
                                            float nhl2e, float wsk, uint32_t (&cnt)[DPT],
@@ -196,19 +197,35 @@ __device__ __forceinline__ void test_draws(const float* sy, const float* sz, int
         load_row<DP>(sy + dn * DP, y);
         float zz[GRAD ? DP : 4];
         if constexpr (GRAD) load_row<DP>(sz + dn * DP, zz);
+        // adjoint: each design's smallest difference is formed one design
+        // ahead (design q + 1's before design q's vote and branch), so that
+        // two designs' dependent chains share a basic block
+        float dnext = 0.0f;
+        if constexpr (GRAD) {
+            float d0[D];
+            diffs<D>(t[0], y, d0);
+            dnext = d0[0];
+#pragma unroll
+            for (int i = 1; i < D; i += 2) dnext = i + 1 < D ? fmin3(dnext, d0[i], d0[i + 1]) : fminf(dnext, d0[i]);
+        }
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             float dif[D];
-            diffs<D>(t[q], y, dif);
             if constexpr (!GRAD) {
+                diffs<D>(t[q], y, dif);
                 uint32_t sgn = 0u;
 #pragma unroll
                 for (int i = 0; i < D; ++i) sgn |= __float_as_uint(dif[i]);
                 cnt[q] += sgn >> 31;
             } else {
-                float dmin = dif[0];
+                const float dmin = dnext;
+                if (q + 1 < NQ) {
+                    float dn1[D];
+                    diffs<D>(t[q + 1 < NQ ? q + 1 : q], y, dn1);   // (index kept in range for the compiler)
+                    dnext = dn1[0];
 #pragma unroll
-                for (int i = 1; i < D; i += 2) dmin = i + 1 < D ? fmin3(dmin, dif[i], dif[i + 1]) : fminf(dmin, dif[i]);
+                    for (int i = 1; i < D; i += 2) dnext = i + 1 < D ? fmin3(dnext, dn1[i], dn1[i + 1]) : fminf(dnext, dn1[i]);
+                }
                 const bool hit = dmin < 0.0f;
                 if constexpr (!SharedShape<D, GRAD>::kCnt) cnt[q] += hit ? 1u : 0u;
                 // sum A over the hits (adding z, or nothing, as the FMA
@@ -225,8 +242,8 @@ __device__ __forceinline__ void test_draws(const float* sy, const float* sz, int
                 {
                     // x_i = (y_i - t_i) log2(e) / h = (t_i - y_i) nhl2e, the
                     // exponent of the sigmoid; the largest is xm = dmin nhl2e
-                    // (nhl2e < 0).  wsk = 25.03 / |nhl2e| (to FP32 rounding), so |dmin| >= wsk
-                    // gives |xm| > 25.02 after rounding.  When xm < -25 (dmin
+                    // (nhl2e < 0).  wsk = 25.03 / |nhl2e| (to FP32
+                    // rounding), so |dmin| >= wsk gives |xm| > 25.02.  When xm < -25 (dmin
                     // >= wsk) every x_i < -25 and the draw adds exactly zero
                     // to every G_i (2^x_i < 2^-25 vanishes in 1 + 2^x_i, so
                     // every keep_i = 1).  When xm > 25 (dmin <= -wsk), keep_k
@@ -239,6 +256,7 @@ __device__ __forceinline__ void test_draws(const float* sy, const float* sz, int
                     // comparison of a magnitude.  wsk < 0 (no sigmoid sums)
                     // never passes.
                     if (__any_sync(0xffffffffu, fabsf(dmin) < wsk)) {
+                        diffs<D>(t[q], y, dif);                    // again, in the rare branch
                         float keep[D], prod = 1.0f;
                         const float2 nh2 = make_float2(nhl2e, nhl2e), one2 = make_float2(1.0f, 1.0f);
 #pragma unroll
