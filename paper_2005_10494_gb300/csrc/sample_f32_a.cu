@@ -1,6 +1,10 @@
 // FP32 sampling kernels, one instantiation per dimension (1,2,3,4,5,6,7,8,9,10).
-// Adjoint kernels of d in 7..12 use the two-blocks-per-SM register bound
-// (measured faster there; at larger d the unbounded kernel is faster).
+// The two-blocks-per-SM register bound (sample_kernel_2b) is used where it
+// measured faster than the unbounded kernel: the adjoint at d = 7..12, 15,
+// 17, 19 and the forward pass at d = 9, 13, 15, 17, 19, whose unbounded
+// kernels take 160-255 registers (one block per SM); elsewhere the bounded
+// kernel spills enough to lose (the adjoint at d = 13, 14, 18, 20: 11-42 %
+// slower) or gains nothing (the forward pass at even d).
 #include "sample.cuh"
 
 namespace mcd {
@@ -15,7 +19,7 @@ const void* sample_kernel_f32_a(int d, bool grad) {
         case 6: return grad ? reinterpret_cast<const void*>(&sample_kernel<6, 6, true, float>) : reinterpret_cast<const void*>(&sample_kernel<6, 6, false, float>);
         case 7: return grad ? reinterpret_cast<const void*>(&sample_kernel_2b<7, 7, true, float>) : reinterpret_cast<const void*>(&sample_kernel<7, 7, false, float>);
         case 8: return grad ? reinterpret_cast<const void*>(&sample_kernel_2b<8, 8, true, float>) : reinterpret_cast<const void*>(&sample_kernel<8, 8, false, float>);
-        case 9: return grad ? reinterpret_cast<const void*>(&sample_kernel_2b<9, 9, true, float>) : reinterpret_cast<const void*>(&sample_kernel<9, 9, false, float>);
+        case 9: return grad ? reinterpret_cast<const void*>(&sample_kernel_2b<9, 9, true, float>) : reinterpret_cast<const void*>(&sample_kernel_2b<9, 9, false, float>);
         case 10: return grad ? reinterpret_cast<const void*>(&sample_kernel_2b<10, 10, true, float>) : reinterpret_cast<const void*>(&sample_kernel<10, 10, false, float>);
         default: return nullptr;
     }
