@@ -616,10 +616,10 @@ def per_design_step(pkg, ctx, args, rates, sm_count, stream, flush):
                       "blocks_per_sm": cfg3["blocks_per_sm"], "tiles": plan.tiles()},
            "roofline": {"bound": "issue", "achieved": achieved / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
                         "frac": achieved / peak_ops, "traffic": traffic_record(plan.tiles()),
-                        "kernel": "sample_kernel<3,3,grad,float>", "kernel_ms": kernel_ms, "ops_per_draw": ops,
+                        "kernel": "sample_kernel_4b<3,3,grad,float>", "kernel_ms": kernel_ms, "ops_per_draw": ops,
                         "peak_basis": "%d SMs x 128 issue slots x %.0f MHz (max SM clock): one warp "
                                       "instruction per scheduler per clock" % (sm_count, SM_MAX_MHZ)},
-           "pipe_bound": {"kernel": "sample_kernel<3,3,grad,float>", "achieved": rate,
+           "pipe_bound": {"kernel": "sample_kernel_4b<3,3,grad,float>", "achieved": rate,
                           "bound": pb["bound_draw_evals_per_s"], "unit": UNIT,
                           "frac": rate / pb["bound_draw_evals_per_s"], "binding": pb["binding"],
                           "sm_clk_per_draw": pb["sm_clk_per_draw"], "ops_per_draw": pb["ops_per_draw"]},

@@ -431,4 +431,18 @@ __global__ void __launch_bounds__(256, 2) sample_kernel_2b(const __grid_constant
     sample_body<DLO, DHI, GRAD, R>(P);
 }
 
+// Three (<= 85 registers) and four (<= 64) resident blocks per SM, for the
+// kernels where that measured faster: the mixed-dimension forward kernel
+// (d = 1..10 in one launch, 1.8 %) and the adjoint at d = 1 (25 %), d = 3
+// (four blocks, 1.9 %) and d = 4 (3 %).
+template <int DLO, int DHI, bool GRAD, typename R>
+__global__ void __launch_bounds__(256, 3) sample_kernel_3b(const __grid_constant__ SampleParams P) {
+    sample_body<DLO, DHI, GRAD, R>(P);
+}
+
+template <int DLO, int DHI, bool GRAD, typename R>
+__global__ void __launch_bounds__(256, 4) sample_kernel_4b(const __grid_constant__ SampleParams P) {
+    sample_body<DLO, DHI, GRAD, R>(P);
+}
+
 }  // namespace mcd

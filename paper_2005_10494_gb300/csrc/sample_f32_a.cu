@@ -5,16 +5,19 @@
 // kernels take 160-255 registers (one block per SM); elsewhere the bounded
 // kernel spills enough to lose (the adjoint at d = 13, 14, 18, 20: 11-42 %
 // slower) or gains nothing (the forward pass at even d).
+// The adjoint at d = 1 and 4 runs three blocks per SM (sample_kernel_3b) and
+// at d = 3 four (sample_kernel_4b); the 3- and 4-block bounds lost at
+// d = 5..8 (11-30 %).
 #include "sample.cuh"
 
 namespace mcd {
 
 const void* sample_kernel_f32_a(int d, bool grad) {
     switch (d) {
-        case 1: return grad ? reinterpret_cast<const void*>(&sample_kernel<1, 1, true, float>) : reinterpret_cast<const void*>(&sample_kernel<1, 1, false, float>);
+        case 1: return grad ? reinterpret_cast<const void*>(&sample_kernel_3b<1, 1, true, float>) : reinterpret_cast<const void*>(&sample_kernel<1, 1, false, float>);
         case 2: return grad ? reinterpret_cast<const void*>(&sample_kernel<2, 2, true, float>) : reinterpret_cast<const void*>(&sample_kernel<2, 2, false, float>);
-        case 3: return grad ? reinterpret_cast<const void*>(&sample_kernel<3, 3, true, float>) : reinterpret_cast<const void*>(&sample_kernel<3, 3, false, float>);
-        case 4: return grad ? reinterpret_cast<const void*>(&sample_kernel<4, 4, true, float>) : reinterpret_cast<const void*>(&sample_kernel<4, 4, false, float>);
+        case 3: return grad ? reinterpret_cast<const void*>(&sample_kernel_4b<3, 3, true, float>) : reinterpret_cast<const void*>(&sample_kernel<3, 3, false, float>);
+        case 4: return grad ? reinterpret_cast<const void*>(&sample_kernel_3b<4, 4, true, float>) : reinterpret_cast<const void*>(&sample_kernel<4, 4, false, float>);
         case 5: return grad ? reinterpret_cast<const void*>(&sample_kernel<5, 5, true, float>) : reinterpret_cast<const void*>(&sample_kernel<5, 5, false, float>);
         case 6: return grad ? reinterpret_cast<const void*>(&sample_kernel<6, 6, true, float>) : reinterpret_cast<const void*>(&sample_kernel<6, 6, false, float>);
         case 7: return grad ? reinterpret_cast<const void*>(&sample_kernel_2b<7, 7, true, float>) : reinterpret_cast<const void*>(&sample_kernel<7, 7, false, float>);

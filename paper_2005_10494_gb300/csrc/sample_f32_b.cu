@@ -5,6 +5,9 @@
 // kernels take 160-255 registers (one block per SM); elsewhere the bounded
 // kernel spills enough to lose (the adjoint at d = 13, 14, 18, 20: 11-42 %
 // slower) or gains nothing (the forward pass at even d).
+// The adjoint at d = 1 and 4 runs three blocks per SM (sample_kernel_3b) and
+// at d = 3 four (sample_kernel_4b); the 3- and 4-block bounds lost at
+// d = 5..8 (11-30 %).
 #include "sample.cuh"
 
 namespace mcd {

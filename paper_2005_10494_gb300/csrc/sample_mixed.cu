@@ -6,7 +6,7 @@ namespace mcd {
 
 const void* sample_kernel_mixed(bool grad) {
     return grad ? reinterpret_cast<const void*>(&sample_kernel_2b<1, kMixedMaxD, true, float>)
-                : reinterpret_cast<const void*>(&sample_kernel<1, kMixedMaxD, false, float>);
+                : reinterpret_cast<const void*>(&sample_kernel_3b<1, kMixedMaxD, false, float>);
 }
 
 }  // namespace mcd
