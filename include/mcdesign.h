@@ -114,9 +114,13 @@ mcd_status mcd_sync_status(mcd_ctx* ctx, mcd_stream stream);
  * see the same draws (common random numbers).  Groups of at least
  * MCD_SHARED_MIN such designs are evaluated by the shared-draw kernel, which
  * makes each draw once per block and tests it against every design of the
- * group: hit counts are bit-identical to the per-design kernel, gradient
- * sums equal up to FP32 rounding.  Smaller groups keep the
- * per-design kernel.  Not with MCD_PLAN_FP64 (MCD_EUNSUPPORTED). */
+ * group: hit counts are bit-identical to the per-design kernel, the
+ * likelihood-ratio sums equal up to FP32 rounding.  The sigmoid sums skip,
+ * warp by warp, the draws whose every contribution is zero or below 3e-8
+ * (no design of the warp within 25 h / log2(e) of the region's boundary in
+ * its smallest margin), which moves the sigmoid gradient's G / N by less
+ * than 3e-8.  Smaller groups keep the per-design kernel.  Not with
+ * MCD_PLAN_FP64 (MCD_EUNSUPPORTED). */
 #define MCD_SHARED_MIN    32
 
 /* Plan a problem.  Reads the HOST arrays (copied), keeps the DEVICE
