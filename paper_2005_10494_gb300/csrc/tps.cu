@@ -12,9 +12,10 @@
 // reflections, Q^T P = [R; 0]: with B = Q^T (K + s I) Q and y~ = Q^T y, the
 // trailing block B22 is positive definite and B22 w = y~_2 gives
 // c = Q [0; w] and R d = y~_1 - B12 w.  B22 is factored by a blocked
-// Cholesky in FP64 (diagonal block in shared memory, panel solve, trailing
-// update), the two triangular systems by row-oriented substitution.  The
-// fitted values at the data are y - s c.
+// Cholesky in FP64 (diagonal block by one warp in registers, panel solve,
+// trailing update), the two triangular systems by block substitution with
+// one multi-block launch per 32 rows.  The fitted values at the data are
+// y - s c.
 //
 // Maximiser.  One block per surface: projected BFGS on -f inside a box
 // (Armijo backtracking along the projected path), started at the data point
@@ -30,7 +31,6 @@ namespace mcd {
 namespace {
 
 constexpr int kNb = 32;            // Cholesky block
-constexpr int kSyrkTile = 64;      // trailing-update tile (64 x 64 outputs per block)
 
 __device__ __forceinline__ double eta(double r, int k) {
     if (k == 1) return r * r * r;
@@ -162,168 +162,248 @@ __global__ void maxabs_kernel(const double* __restrict__ A, int64_t count, unsig
 }
 
 // Cholesky of the b x b diagonal block at G (leading dimension ld), lower,
-// in place.  A pivot at or below n eps max|A| (the projected system is
-// singular to working precision, e.g. repeated points without smoothing)
-// sets *bad.
-__global__ void __launch_bounds__(kNb * kNb) chol_diag_kernel(double* __restrict__ G, int64_t ld, int b, int n,
-                                                             const unsigned long long* __restrict__ amax,
-                                                             int* __restrict__ bad) {
-    __shared__ double a[kNb][kNb + 1];
-    const int tx = threadIdx.x % kNb, ty = threadIdx.x / kNb;   // column tx, row ty
+// in place, by one warp: lane i holds row i of the block in registers.  For
+// column c the pivot comes from lane c by a shuffle, the lanes below it scale
+// their entry by its reciprocal square root, and each later column j takes
+// L_jc from lane j by a shuffle for the update A_ij -= L_ic L_jc (i >= j).
+// A pivot at or below n eps max|A| (the projected system is singular to
+// working precision, e.g. repeated points without smoothing) sets *bad.
+__global__ void __launch_bounds__(32) chol_diag_kernel(double* __restrict__ G, int64_t ld, int b, int n,
+                                                      const unsigned long long* __restrict__ amax,
+                                                      int* __restrict__ bad) {
+    const int i = threadIdx.x;
     const double floor_p = static_cast<double>(n) * 2.220446049250313e-16 * __longlong_as_double(static_cast<long long>(*amax));
-    if (ty < b && tx < b) a[ty][tx] = G[static_cast<int64_t>(ty) * ld + tx];
-    __syncthreads();
-    __shared__ double inv;
-    for (int kk = 0; kk < b; ++kk) {
-        if (threadIdx.x == 0) {
-            const double p = a[kk][kk];
-            if (!(p > floor_p)) { *bad = 1; a[kk][kk] = 1.0; inv = 1.0; }
-            else { const double r = sqrt(p); a[kk][kk] = r; inv = 1.0 / r; }
+    double a[kNb];
+#pragma unroll
+    for (int j = 0; j < kNb; ++j) a[j] = (i < b && j <= i) ? G[static_cast<int64_t>(i) * ld + j] : 0.0;
+    bool failed = false;
+#pragma unroll
+    for (int c = 0; c < kNb; ++c) {
+        if (c < b) {                                          // b is warp-uniform
+            const double p = __shfl_sync(0xffffffffu, a[c], c);
+            double r = 1.0, inv = 1.0;
+            if (p > floor_p) { inv = rsqrt(p); r = p * inv; }
+            else failed = true;
+            if (i == c) a[c] = r;
+            else if (i > c) a[c] *= inv;
+#pragma unroll
+            for (int j = c + 1; j < kNb; ++j) {
+                const double ljc = __shfl_sync(0xffffffffu, a[c], j);
+                if (i >= j) a[j] = fma(-a[c], ljc, a[j]);
+            }
         }
-        __syncthreads();
-        if (tx == kk && ty > kk && ty < b) a[ty][kk] *= inv;
-        __syncthreads();
-        if (ty > kk && tx > kk && tx <= ty && ty < b) a[ty][tx] -= a[ty][kk] * a[tx][kk];
-        __syncthreads();
     }
-    if (ty < b && tx <= ty) G[static_cast<int64_t>(ty) * ld + tx] = a[ty][tx];
+    if (failed && i == 0) *bad = 1;
+    if (i < b) {
+#pragma unroll
+        for (int j = 0; j < kNb; ++j)
+            if (j <= i) G[static_cast<int64_t>(i) * ld + j] = a[j];
+    }
 }
 
 // Rows below the diagonal block: X <- X L^{-T} for the n_rem x b panel at
-// Pn (leading dimension ld), L the factored diagonal block at G.
-__global__ void chol_trsm_kernel(const double* __restrict__ G, double* __restrict__ Pn, int64_t ld, int b, int n_rem) {
+// Pn (leading dimension ld), L the factored diagonal block at G; one row per
+// thread.  Column by column, x_c = s_c / L_cc (the pivots' reciprocals
+// formed once per block) and s_j -= x_c L_jc for the later columns, so the
+// dependent chain is one multiply and one FMA per column and the updates of
+// a column are independent.
+constexpr int kTrsmThreads = 64;
+__global__ void __launch_bounds__(kTrsmThreads) chol_trsm_kernel(const double* __restrict__ G,
+                                                                 double* __restrict__ Pn, int64_t ld, int b,
+                                                                 int n_rem) {
     __shared__ double L[kNb][kNb + 1];
+    __shared__ double rd[kNb];
     for (int t = threadIdx.x; t < kNb * kNb; t += blockDim.x) {
         const int r = t / kNb, c = t % kNb;
         L[r][c] = (r < b && c <= r) ? G[static_cast<int64_t>(r) * ld + c] : 0.0;
     }
     __syncthreads();
+    if (threadIdx.x < kNb) rd[threadIdx.x] = threadIdx.x < b ? 1.0 / L[threadIdx.x][threadIdx.x] : 0.0;
+    __syncthreads();
     const int row = blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= n_rem) return;
     double* p = Pn + static_cast<int64_t>(row) * ld;
-    double xr[kNb];
+    double x[kNb];
 #pragma unroll
-    for (int j = 0; j < kNb; ++j) {
-        if (j < b) {
-            double s = p[j];
+    for (int c = 0; c < kNb; ++c) x[c] = c < b ? p[c] : 0.0;
 #pragma unroll
-            for (int l = 0; l < j; ++l) s -= xr[l] * L[j][l];
-            xr[j] = s / L[j][j];
-        }
+    for (int c = 0; c < kNb; ++c) {
+        x[c] *= rd[c];
+#pragma unroll
+        for (int j2 = c + 1; j2 < kNb; ++j2) x[j2] = fma(-x[c], L[j2][c], x[j2]);
     }
 #pragma unroll
-    for (int j = 0; j < kNb; ++j)
-        if (j < b) p[j] = xr[j];
+    for (int c = 0; c < kNb; ++c)
+        if (c < b) p[c] = x[c];
 }
 
 // Trailing update of the lower triangle: T[i][j] -= sum_l Pn[i][l] Pn[j][l],
 // i >= j, for the n_rem x n_rem matrix at T and the n_rem x b panel at Pn.
-// Block (bx, by): output tile rows by*64.., columns bx*64..; 256 threads,
-// 4 x 4 outputs each.
+// Block (bx, by): output tile rows by*TS.., columns bx*TS..; 256 threads,
+// P x P outputs each (TS = 16 P).  64 x 64 tiles while there are enough of
+// them to fill the GPU, 32 x 32 below that (a tile's FMAs run on one SM's
+// FP64 units, about two a clock).
+template <int P>
 __global__ void __launch_bounds__(256) chol_syrk_kernel(double* __restrict__ T, const double* __restrict__ Pn,
                                                         int64_t ld, int b, int n_rem) {
+    constexpr int TS = 16 * P;
     const int ti = blockIdx.y, tj = blockIdx.x;
     if (tj > ti) return;
-    __shared__ double si[kSyrkTile][kNb + 1];
-    __shared__ double sj[kSyrkTile][kNb + 1];
-    const int r0 = ti * kSyrkTile, c0 = tj * kSyrkTile;
-    for (int t = threadIdx.x; t < kSyrkTile * kNb; t += blockDim.x) {
+    __shared__ double si[TS][kNb + 1];
+    __shared__ double sj[TS][kNb + 1];
+    const int r0 = ti * TS, c0 = tj * TS;
+    for (int t = threadIdx.x; t < TS * kNb; t += blockDim.x) {
         const int r = t / kNb, l = t % kNb;
         si[r][l] = (r0 + r < n_rem && l < b) ? Pn[static_cast<int64_t>(r0 + r) * ld + l] : 0.0;
         sj[r][l] = (c0 + r < n_rem && l < b) ? Pn[static_cast<int64_t>(c0 + r) * ld + l] : 0.0;
     }
     __syncthreads();
     const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
-    double acc[4][4] = {};
+    double acc[P][P] = {};
     for (int l = 0; l < b; ++l) {
-        double a[4], c[4];
+        double a[P], c[P];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) { a[q] = si[ty + 16 * q][l]; c[q] = sj[tx + 16 * q][l]; }
+        for (int q = 0; q < P; ++q) { a[q] = si[ty + 16 * q][l]; c[q] = sj[tx + 16 * q][l]; }
 #pragma unroll
-        for (int p = 0; p < 4; ++p)
+        for (int p = 0; p < P; ++p)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[p][q] = fma(a[p], c[q], acc[p][q]);
+            for (int q = 0; q < P; ++q) acc[p][q] = fma(a[p], c[q], acc[p][q]);
     }
 #pragma unroll
-    for (int p = 0; p < 4; ++p)
+    for (int p = 0; p < P; ++p)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < P; ++q) {
             const int i = r0 + ty + 16 * p, j = c0 + tx + 16 * q;
             if (i < n_rem && j < n_rem && j <= i) T[static_cast<int64_t>(i) * ld + j] -= acc[p][q];
         }
 }
 
-// Solve L z = r then L^T w = z in place, n x n lower factor at L (leading
-// dimension ld), one block of 32 warps, 32 rows at a time.  Forward: warp r
-// forms row r's product with the solved entries (rows of L read
-// contiguously), then warp 0 solves the 32 x 32 diagonal block with
-// shuffles.  Backward: warp 0 solves the transposed diagonal block, then all
-// threads subtract the block's contribution from the earlier entries
-// (again reading rows of L).
-constexpr int kSolveThreads = 1024;
-__global__ void __launch_bounds__(kSolveThreads) chol_solve_kernel(const double* __restrict__ L, int64_t ld, int n,
-                                                                  double* __restrict__ z) {
-    __shared__ double part[32];
-    extern __shared__ double dinv[];                          // 1 / L_ii, n entries
+// Solve L z = r, then L^T w = z, for the n x n lower factor at L (leading
+// dimension ld), right-looking, one launch per block of 32 rows so that
+// every SM's FP64 units share the n^2 multiply-adds.  GB300 issues about two
+// FP64 FMAs per SM clock; a single block doing all of them was bound by its
+// one SM.
+//   Forward step at rows i0..i0+b-1: every block solves the b x b diagonal
+//   system L_bb z_b = r_b with one warp (lane q holds row q of L_bb, r_q
+//   and 1 / L_qq in registers; column by column, z_c comes from lane c by
+//   a shuffle and every lane subtracts L_qc z_c, so no step waits on a
+//   memory load or a reduction) into shared memory, block 0 stores z_b,
+//   then the block's warps update the later rows it owns, r_j -= L_j,b z_b,
+//   one row per warp (its 32 entries of L contiguous).
+//   Backward step: the transposed diagonal system L_bb^T w_b = z_b (lane q
+//   holds column q of L_bb, from the last column back), then
+//   z_j -= sum_c L_(i0+c),j w_c for the earlier rows, one per thread
+//   (rows of L read contiguously across the warp).
+// The right-hand side is read and updated in one array and the solution is
+// written to another, so that no block reads an entry another block of the
+// same launch writes.
+constexpr int kSolveThreads = 256;
+constexpr int kSolveMaxBlocks = 512;     // blocks per step (each re-solves the 32 x 32 diagonal)
+
+__global__ void recip_diag_kernel(const double* __restrict__ L, int64_t ld, int n, double* __restrict__ dinv) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dinv[i] = 1.0 / L[static_cast<int64_t>(i) * ld + i];
+}
+
+__global__ void __launch_bounds__(kSolveThreads) solve_fwd_step_kernel(const double* __restrict__ L, int64_t ld,
+                                                                      int n, int i0,
+                                                                      const double* __restrict__ dinv,
+                                                                      double* __restrict__ r,
+                                                                      double* __restrict__ z) {
+    __shared__ double zb[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) dinv[i] = 1.0 / L[static_cast<int64_t>(i) * ld + i];
-    __syncthreads();
-    for (int i0 = 0; i0 < n; i0 += 32) {
-        const int b = n - i0 < 32 ? n - i0 : 32;
-        if (warp < b) {
-            const double* row = L + static_cast<int64_t>(i0 + warp) * ld;
-            double s = 0.0;
-            for (int j = lane; j < i0; j += 32) s += row[j] * z[j];
-            for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) part[warp] = z[i0 + warp] - s;
-        }
-        __syncthreads();
-        if (warp == 0) {
-            double zc = 0.0;                                   // lane c holds z[i0 + c] once solved
-            for (int r = 0; r < b; ++r) {
-                const double lrc = lane < r ? L[static_cast<int64_t>(i0 + r) * ld + i0 + lane] : 0.0;
-                double t = lrc * zc;
-                for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-                const double zr = (part[r] - t) * dinv[i0 + r];
-                if (lane == r) zc = zr;
+    const int b = n - i0 < 32 ? n - i0 : 32;
+    if (warp == 0) {
+        // lane q: row q of the diagonal block left of the diagonal, its
+        // right-hand side and reciprocal pivot, all loaded up front; then
+        // column by column, z_c = r_c / L_cc from lane c and r_q -= L_qc z_c
+        double lrow[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+            lrow[c] = (lane < b && c < lane) ? L[static_cast<int64_t>(i0 + lane) * ld + i0 + c] : 0.0;
+        double rq = lane < b ? r[i0 + lane] : 0.0;
+        const double dq = lane < b ? dinv[i0 + lane] : 0.0;
+        double zq = 0.0;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+            if (c < b) {                                         // b is warp-uniform
+                const double zc = __shfl_sync(0xffffffffu, rq * dq, c);
+                if (lane == c) zq = zc;
+                rq = fma(-lrow[c], zc, rq);
             }
-            if (lane < b) z[i0 + lane] = zc;
         }
-        __syncthreads();
+        zb[lane] = zq;
+        if (blockIdx.x == 0 && lane < b) z[i0 + lane] = zq;
     }
-    const int nblk = (n + 31) / 32;
-    for (int bi = nblk - 1; bi >= 0; --bi) {
-        const int i0 = bi * 32;
-        const int b = n - i0 < 32 ? n - i0 : 32;
-        if (warp == 0) {
-            double wc = 0.0;                                   // lane c holds w[i0 + c] once solved
-            for (int r = b - 1; r >= 0; --r) {
-                const double lcr = (lane > r && lane < b) ? L[static_cast<int64_t>(i0 + lane) * ld + i0 + r] : 0.0;
-                double t = lcr * wc;
-                for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-                const double wr = (z[i0 + r] - t) * dinv[i0 + r];
-                if (lane == r) wc = wr;
-            }
-            if (lane < b) z[i0 + lane] = wc;
-        }
-        __syncthreads();
-        for (int j = threadIdx.x; j < i0; j += blockDim.x) {
-            double s = 0.0;
-            for (int r = 0; r < b; ++r) s += L[static_cast<int64_t>(i0 + r) * ld + j] * z[i0 + r];
-            z[j] -= s;
-        }
-        __syncthreads();
+    __syncthreads();
+    const int warps = blockDim.x >> 5;
+    for (int j = i0 + b + blockIdx.x * warps + warp; j < n; j += gridDim.x * warps) {
+        double t = lane < b ? L[static_cast<int64_t>(j) * ld + i0 + lane] * zb[lane] : 0.0;
+        for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) r[j] -= t;
     }
 }
 
-// The two triangular solves with L (n <= 16384: the reciprocals of the
-// diagonal, 8 n bytes, in dynamic shared memory).
-cudaError_t launch_solve(const double* L, int64_t ld, int n, double* z, cudaStream_t stream) {
-    const size_t smem = sizeof(double) * static_cast<size_t>(n);
-    cudaError_t e = cudaFuncSetAttribute(chol_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    chol_solve_kernel<<<1, kSolveThreads, smem, stream>>>(L, ld, n, z);
+__global__ void __launch_bounds__(kSolveThreads) solve_bwd_step_kernel(const double* __restrict__ L, int64_t ld,
+                                                                      int n, int i0,
+                                                                      const double* __restrict__ dinv,
+                                                                      double* __restrict__ z,
+                                                                      double* __restrict__ w) {
+    __shared__ double wb[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int b = n - i0 < 32 ? n - i0 : 32;
+    if (warp == 0) {
+        // lane q: column q of the diagonal block below the diagonal (rows of
+        // L read contiguously across the warp); then from the last column
+        // back, w_c = z_c / L_cc from lane c and z_q -= L_cq w_c
+        double lcol[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+            lcol[c] = (c < b && lane < c) ? L[static_cast<int64_t>(i0 + c) * ld + i0 + lane] : 0.0;
+        double zq = lane < b ? z[i0 + lane] : 0.0;
+        const double dq = lane < b ? dinv[i0 + lane] : 0.0;
+        double wq = 0.0;
+#pragma unroll
+        for (int c = 31; c >= 0; --c) {
+            if (c < b) {
+                const double wc = __shfl_sync(0xffffffffu, zq * dq, c);
+                if (lane == c) wq = wc;
+                zq = fma(-lcol[c], wc, zq);
+            }
+        }
+        wb[lane] = wq;
+        if (blockIdx.x == 0 && lane < b) w[i0 + lane] = wq;
+    }
+    __syncthreads();
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < i0; j += gridDim.x * blockDim.x) {
+        double t = 0.0;
+        for (int c = 0; c < b; ++c) t = fma(L[static_cast<int64_t>(i0 + c) * ld + j], wb[c], t);
+        z[j] -= t;
+    }
+}
+
+// The two triangular solves with L: the right-hand side in z on entry and
+// the solution in z on return; r2 (n doubles) holds the intermediate
+// solution and dinv (n doubles) the reciprocals of L's diagonal.
+cudaError_t launch_solve(const double* L, int64_t ld, int n, double* z, double* r2, double* dinv,
+                         cudaStream_t stream) {
+    if (n <= 0) return cudaSuccess;
+    recip_diag_kernel<<<(n + 255) / 256, 256, 0, stream>>>(L, ld, n, dinv);
+    const int nblk = (n + 31) / 32;
+    for (int bi = 0; bi < nblk; ++bi) {
+        const int i0 = bi * 32;
+        const int rows = n - i0 - 32;                            // later rows to update
+        const int warps = kSolveThreads / 32;
+        int grid = rows > 0 ? (rows + warps - 1) / warps : 1;
+        if (grid > kSolveMaxBlocks) grid = kSolveMaxBlocks;
+        solve_fwd_step_kernel<<<grid, kSolveThreads, 0, stream>>>(L, ld, n, i0, dinv, z, r2);
+    }
+    for (int bi = nblk - 1; bi >= 0; --bi) {
+        const int i0 = bi * 32;
+        int grid = i0 > 0 ? (i0 + kSolveThreads - 1) / kSolveThreads : 1;
+        if (grid > kSolveMaxBlocks) grid = kSolveMaxBlocks;
+        solve_bwd_step_kernel<<<grid, kSolveThreads, 0, stream>>>(L, ld, n, i0, dinv, r2, z);
+    }
     return cudaGetLastError();
 }
 
@@ -610,24 +690,38 @@ __global__ void __launch_bounds__(kMaxThreads) argmax_tps_kernel(const double* _
 // Blocked Cholesky (lower, in place) of the n x n matrix at B (leading
 // dimension ld).
 static void chol_blocked(double* B, int64_t ld, int n, const unsigned long long* amax, int* bad, cudaStream_t stream) {
+    // 64 x 64 trailing-update tiles while their lower triangle has at least
+    // one tile per SM, 32 x 32 after that
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms = 1;
     for (int j0 = 0; j0 < n; j0 += kNb) {
         const int b = n - j0 < kNb ? n - j0 : kNb;
         double* G = B + j0 * ld + j0;
-        chol_diag_kernel<<<1, kNb * kNb, 0, stream>>>(G, ld, b, n, amax, bad);
+        chol_diag_kernel<<<1, 32, 0, stream>>>(G, ld, b, n, amax, bad);
         const int rem = n - j0 - b;
         if (rem > 0) {
             double* Pn = G + b * ld;
-            chol_trsm_kernel<<<(rem + 127) / 128, 128, 0, stream>>>(G, Pn, ld, b, rem);
-            const int tiles = (rem + kSyrkTile - 1) / kSyrkTile;
-            chol_syrk_kernel<<<dim3(tiles, tiles), 256, 0, stream>>>(Pn + b, Pn, ld, b, rem);
+            chol_trsm_kernel<<<(rem + kTrsmThreads - 1) / kTrsmThreads, kTrsmThreads, 0, stream>>>(G, Pn, ld, b, rem);
+            const int t64 = (rem + 63) / 64;
+            if (t64 * (t64 + 1) / 2 >= sms) {
+                chol_syrk_kernel<4><<<dim3(t64, t64), 256, 0, stream>>>(Pn + b, Pn, ld, b, rem);
+            } else {
+                const int t32 = (rem + 31) / 32;
+                chol_syrk_kernel<2><<<dim3(t32, t32), 256, 0, stream>>>(Pn + b, Pn, ld, b, rem);
+            }
         }
     }
 }
 
-size_t tps_workspace_doubles(int N, int k) {
+// Workspace of one fit: A (N x N), V and Pw (m x N each), y~, w, z (N each),
+// R (m x m), tau (m), then the reciprocals of the factor's diagonal (N).
+static size_t tps_base_doubles(int N, int k) {
     const size_t m = static_cast<size_t>(k) + 1;
     return static_cast<size_t>(N) * N + 2 * m * N + 3 * static_cast<size_t>(N) + m * m + m + 8;
 }
+
+size_t tps_workspace_doubles(int N, int k) { return tps_base_doubles(N, k) + static_cast<size_t>(N); }
 
 cudaError_t tps_fit_one(const double* x, const double* y, int N, int k, double s, double* coef, double* fitted,
                         double* ws, int* bad, unsigned long long* amax, DevStatus* status, int surf,
@@ -660,7 +754,7 @@ cudaError_t tps_fit_one(const double* x, const double* y, int N, int k, double s
     chol_blocked(B, N, n, amax, bad, stream);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(z, yt + m, sizeof(double) * n, cudaMemcpyDeviceToDevice, stream)) != cudaSuccess) return e;
-    if ((e = launch_solve(B, N, n, z, stream)) != cudaSuccess) return e;
+    if ((e = launch_solve(B, N, n, z, w, ws + tps_base_doubles(N, k), stream)) != cudaSuccess) return e;
     combine_kernel<<<1, 1024, 0, stream>>>(A, V, tau, R, yt, z, y, N, k, s, bad, coef, fitted, status, surf);
     return cudaGetLastError();
 }
@@ -707,7 +801,7 @@ cudaError_t tps_gcv(const double* x, const double* y, int N, int k, const double
         chol_blocked(W, n, n, amax, bad, stream);
         if ((e = cudaMemcpyAsync(z, yt + m, sizeof(double) * n, cudaMemcpyDeviceToDevice, stream)) != cudaSuccess)
             return e;
-        if ((e = launch_solve(W, n, n, z, stream)) != cudaSuccess) return e;
+        if ((e = launch_solve(W, n, n, z, w, ws + tps_base_doubles(N, k), stream)) != cudaSuccess) return e;
         tri_inv_diag_kernel<<<nb, kNb, 0, stream>>>(W, X, n);
         for (int bi = 1; bi < nb; ++bi) tri_inv_step_kernel<<<bi, 256, 0, stream>>>(W, X, n, bi);
         sumsq_lower_kernel<<<n, 128, 0, stream>>>(X, n, trace);
