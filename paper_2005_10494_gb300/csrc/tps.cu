@@ -161,21 +161,15 @@ __global__ void maxabs_kernel(const double* __restrict__ A, int64_t count, unsig
     if ((threadIdx.x & 31) == 0) atomicMax(out, static_cast<unsigned long long>(__double_as_longlong(m)));
 }
 
-// Cholesky of the b x b diagonal block at G (leading dimension ld), lower,
-// in place, by one warp: lane i holds row i of the block in registers.  For
-// column c the pivot comes from lane c by a shuffle, the lanes below it scale
-// their entry by its reciprocal square root, and each later column j takes
-// L_jc from lane j by a shuffle for the update A_ij -= L_ic L_jc (i >= j).
-// A pivot at or below n eps max|A| (the projected system is singular to
-// working precision, e.g. repeated points without smoothing) sets *bad.
-__global__ void __launch_bounds__(32) chol_diag_kernel(double* __restrict__ G, int64_t ld, int b, int n,
-                                                      const unsigned long long* __restrict__ amax,
-                                                      int* __restrict__ bad) {
-    const int i = threadIdx.x;
-    const double floor_p = static_cast<double>(n) * 2.220446049250313e-16 * __longlong_as_double(static_cast<long long>(*amax));
-    double a[kNb];
-#pragma unroll
-    for (int j = 0; j < kNb; ++j) a[j] = (i < b && j <= i) ? G[static_cast<int64_t>(i) * ld + j] : 0.0;
+// Cholesky of a b x b diagonal block held by one warp, lane i holding row i
+// (a[j], j <= i) in registers, in place.  For column c the pivot comes from
+// lane c by a shuffle, the lanes below it scale their entry by its
+// reciprocal square root, and each later column j takes L_jc from lane j by
+// a shuffle for the update A_ij -= L_ic L_jc (i >= j).  A pivot at or below
+// floor_p (the projected system is singular to working precision, e.g.
+// repeated points without smoothing) is replaced by 1 and reported.
+__device__ __forceinline__ bool factor_rows(double (&a)[kNb], int b, double floor_p) {
+    const int i = threadIdx.x & 31;
     bool failed = false;
 #pragma unroll
     for (int c = 0; c < kNb; ++c) {
@@ -193,11 +187,68 @@ __global__ void __launch_bounds__(32) chol_diag_kernel(double* __restrict__ G, i
             }
         }
     }
-    if (failed && i == 0) *bad = 1;
+    return failed;
+}
+
+__device__ __forceinline__ double pivot_floor(int n, const unsigned long long* amax) {
+    return static_cast<double>(n) * 2.220446049250313e-16 * __longlong_as_double(static_cast<long long>(*amax));
+}
+
+// The first diagonal block of the factorisation (G, leading dimension ld).
+__global__ void __launch_bounds__(32) chol_diag_kernel(double* __restrict__ G, int64_t ld, int b, int n,
+                                                      const unsigned long long* __restrict__ amax,
+                                                      int* __restrict__ bad) {
+    const int i = threadIdx.x;
+    double a[kNb];
+#pragma unroll
+    for (int j = 0; j < kNb; ++j) a[j] = (i < b && j <= i) ? G[static_cast<int64_t>(i) * ld + j] : 0.0;
+    if (factor_rows(a, b, pivot_floor(n, amax)) && i == 0) *bad = 1;
     if (i < b) {
 #pragma unroll
         for (int j = 0; j < kNb; ++j)
             if (j <= i) G[static_cast<int64_t>(i) * ld + j] = a[j];
+    }
+}
+
+// Look-ahead: the next diagonal block (the bn x bn block at T, leading
+// dimension ld) receives its update from the current panel Pn (its first bn
+// rows, b columns), by all 256 threads, and is then factored by one warp,
+// while the trailing update of the rest of the matrix runs on another
+// stream (chol_syrk_kernel skips this block).
+constexpr int kNextThreads = 256;
+__global__ void __launch_bounds__(kNextThreads) chol_next_diag_kernel(double* __restrict__ T,
+                                                                     const double* __restrict__ Pn, int64_t ld,
+                                                                     int b, int bn, int n,
+                                                                     const unsigned long long* __restrict__ amax,
+                                                                     int* __restrict__ bad) {
+    __shared__ double pr[kNb][kNb + 1];
+    __shared__ double tb[kNb][kNb + 1];
+    for (int t = threadIdx.x; t < kNb * kNb; t += blockDim.x) {
+        const int r = t / kNb, c = t % kNb;
+        pr[r][c] = (r < bn && c < b) ? Pn[static_cast<int64_t>(r) * ld + c] : 0.0;
+        tb[r][c] = (r < bn && c <= r) ? T[static_cast<int64_t>(r) * ld + c] : 0.0;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < kNb * kNb; t += blockDim.x) {
+        const int r = t / kNb, c = t % kNb;
+        if (r < bn && c <= r) {
+            double acc = 0.0;
+#pragma unroll
+            for (int l = 0; l < kNb; ++l) acc = fma(pr[r][l], pr[c][l], acc);
+            tb[r][c] -= acc;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x >= 32) return;
+    const int i = threadIdx.x;
+    double a[kNb];
+#pragma unroll
+    for (int j = 0; j < kNb; ++j) a[j] = tb[i][j];
+    if (factor_rows(a, bn, pivot_floor(n, amax)) && i == 0) *bad = 1;
+    if (i < bn) {
+#pragma unroll
+        for (int j = 0; j < kNb; ++j)
+            if (j <= i) T[static_cast<int64_t>(i) * ld + j] = a[j];
     }
 }
 
@@ -242,10 +293,12 @@ __global__ void __launch_bounds__(kTrsmThreads) chol_trsm_kernel(const double* _
 // Block (bx, by): output tile rows by*TS.., columns bx*TS..; 256 threads,
 // P x P outputs each (TS = 16 P).  64 x 64 tiles while there are enough of
 // them to fill the GPU, 32 x 32 below that (a tile's FMAs run on one SM's
-// FP64 units, about two a clock).
+// FP64 units, about two a clock).  The leading skip x skip block (the next
+// diagonal block, updated and factored by chol_next_diag_kernel meanwhile)
+// is left alone.
 template <int P>
 __global__ void __launch_bounds__(256) chol_syrk_kernel(double* __restrict__ T, const double* __restrict__ Pn,
-                                                        int64_t ld, int b, int n_rem) {
+                                                        int64_t ld, int b, int n_rem, int skip) {
     constexpr int TS = 16 * P;
     const int ti = blockIdx.y, tj = blockIdx.x;
     if (tj > ti) return;
@@ -274,7 +327,8 @@ __global__ void __launch_bounds__(256) chol_syrk_kernel(double* __restrict__ T, 
 #pragma unroll
         for (int q = 0; q < P; ++q) {
             const int i = r0 + ty + 16 * p, j = c0 + tx + 16 * q;
-            if (i < n_rem && j < n_rem && j <= i) T[static_cast<int64_t>(i) * ld + j] -= acc[p][q];
+            if (i < n_rem && j < n_rem && j <= i && !(i < skip && j < skip))
+                T[static_cast<int64_t>(i) * ld + j] -= acc[p][q];
         }
 }
 
@@ -688,30 +742,58 @@ __global__ void __launch_bounds__(kMaxThreads) argmax_tps_kernel(const double* _
 }  // namespace
 
 // Blocked Cholesky (lower, in place) of the n x n matrix at B (leading
-// dimension ld).
-static void chol_blocked(double* B, int64_t ld, int n, const unsigned long long* amax, int* bad, cudaStream_t stream) {
+// dimension ld), with one step of look-ahead: after the panel solve of
+// block j, the next diagonal block is updated and factored on a second
+// stream while the rest of the trailing update runs on `stream`; the two
+// write disjoint parts of the matrix, and the next panel solve waits for
+// both.  The factorisation of a diagonal block is a chain of 32 dependent
+// FP64 pivots (about 1.5 us each on this GPU's FP64 units), which the
+// trailing update now hides.
+static cudaError_t chol_blocked(double* B, int64_t ld, int n, const unsigned long long* amax, int* bad,
+                                cudaStream_t stream) {
     // 64 x 64 trailing-update tiles while their lower triangle has at least
     // one tile per SM, 32 x 32 after that
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         sms = 1;
-    for (int j0 = 0; j0 < n; j0 += kNb) {
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_panel = nullptr, ev_diag = nullptr;
+    int prio_lo = 0, prio_hi = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, prio_hi);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_panel, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_diag, cudaEventDisableTiming);
+    if (e == cudaSuccess && n > 0) {
+        const int b0 = n < kNb ? n : kNb;
+        chol_diag_kernel<<<1, 32, 0, stream>>>(B, ld, b0, n, amax, bad);
+    }
+    for (int j0 = 0; e == cudaSuccess && j0 < n; j0 += kNb) {
         const int b = n - j0 < kNb ? n - j0 : kNb;
         double* G = B + j0 * ld + j0;
-        chol_diag_kernel<<<1, 32, 0, stream>>>(G, ld, b, n, amax, bad);
         const int rem = n - j0 - b;
-        if (rem > 0) {
-            double* Pn = G + b * ld;
-            chol_trsm_kernel<<<(rem + kTrsmThreads - 1) / kTrsmThreads, kTrsmThreads, 0, stream>>>(G, Pn, ld, b, rem);
-            const int t64 = (rem + 63) / 64;
-            if (t64 * (t64 + 1) / 2 >= sms) {
-                chol_syrk_kernel<4><<<dim3(t64, t64), 256, 0, stream>>>(Pn + b, Pn, ld, b, rem);
-            } else {
-                const int t32 = (rem + 31) / 32;
-                chol_syrk_kernel<2><<<dim3(t32, t32), 256, 0, stream>>>(Pn + b, Pn, ld, b, rem);
-            }
+        if (rem <= 0) break;
+        double* Pn = G + b * ld;
+        chol_trsm_kernel<<<(rem + kTrsmThreads - 1) / kTrsmThreads, kTrsmThreads, 0, stream>>>(G, Pn, ld, b, rem);
+        const int bn = rem < kNb ? rem : kNb;
+        if ((e = cudaEventRecord(ev_panel, stream)) != cudaSuccess) break;
+        if ((e = cudaStreamWaitEvent(side, ev_panel, 0)) != cudaSuccess) break;
+        chol_next_diag_kernel<<<1, kNextThreads, 0, side>>>(Pn + b, Pn, ld, b, bn, n, amax, bad);
+        if ((e = cudaEventRecord(ev_diag, side)) != cudaSuccess) break;
+        const int t64 = (rem + 63) / 64;
+        if (t64 * (t64 + 1) / 2 >= sms) {
+            chol_syrk_kernel<4><<<dim3(t64, t64), 256, 0, stream>>>(Pn + b, Pn, ld, b, rem, bn);
+        } else {
+            const int t32 = (rem + 31) / 32;
+            chol_syrk_kernel<2><<<dim3(t32, t32), 256, 0, stream>>>(Pn + b, Pn, ld, b, rem, bn);
         }
+        if ((e = cudaStreamWaitEvent(stream, ev_diag, 0)) != cudaSuccess) break;
     }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    // destruction is deferred by the runtime until the queued work is done
+    if (ev_diag) cudaEventDestroy(ev_diag);
+    if (ev_panel) cudaEventDestroy(ev_panel);
+    if (side) cudaStreamDestroy(side);
+    return e;
 }
 
 // Workspace of one fit: A (N x N), V and Pw (m x N each), y~, w, z (N each),
@@ -751,8 +833,7 @@ cudaError_t tps_fit_one(const double* x, const double* y, int N, int k, double s
     const int n = N - m;
     double* B = A + static_cast<size_t>(m) * N + m;
     maxabs_kernel<<<256, 256, 0, stream>>>(A, static_cast<int64_t>(N) * N, amax);
-    chol_blocked(B, N, n, amax, bad, stream);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = chol_blocked(B, N, n, amax, bad, stream)) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(z, yt + m, sizeof(double) * n, cudaMemcpyDeviceToDevice, stream)) != cudaSuccess) return e;
     if ((e = launch_solve(B, N, n, z, w, ws + tps_base_doubles(N, k), stream)) != cudaSuccess) return e;
     combine_kernel<<<1, 1024, 0, stream>>>(A, V, tau, R, yt, z, y, N, k, s, bad, coef, fitted, status, surf);
@@ -798,7 +879,7 @@ cudaError_t tps_gcv(const double* x, const double* y, int N, int k, const double
         if ((e = cudaMemsetAsync(X, 0, sizeof(double) * static_cast<size_t>(n) * n, stream)) != cudaSuccess) return e;
         shift_copy_kernel<<<dim3((n + 255) / 256, n), 256, 0, stream>>>(T22, N, W, n, s_values[q]);
         maxabs_kernel<<<256, 256, 0, stream>>>(W, static_cast<int64_t>(n) * n, amax);
-        chol_blocked(W, n, n, amax, bad, stream);
+        if ((e = chol_blocked(W, n, n, amax, bad, stream)) != cudaSuccess) return e;
         if ((e = cudaMemcpyAsync(z, yt + m, sizeof(double) * n, cudaMemcpyDeviceToDevice, stream)) != cudaSuccess)
             return e;
         if ((e = launch_solve(W, n, n, z, w, ws + tps_base_doubles(N, k), stream)) != cudaSuccess) return e;
