@@ -277,7 +277,9 @@ mcd_status mc_fwer_calibrate(mcd_ctx* ctx, const mcd_problem* prob, const double
  * definite after the projection (repeated points with smoothing 0) gives NaN
  * outputs for that surface and MCD_ENOTSPD with its index at mcd_sync_status.
  * Workspace n_pts^2 doubles, allocated and freed in stream order; not for use
- * under stream capture. */
+ * under stream capture.  The factorisation also runs kernels on a stream of
+ * its own, joined to `stream` by events, so all of the call's work is done
+ * when the work queued on `stream` is. */
 mcd_status mc_tps_fit(mcd_ctx* ctx, int32_t n_surf, int32_t n_pts, int32_t k, const double* x,
                       const double* y, double smoothing, double* coef, double* fitted, mcd_stream stream);
 
@@ -291,7 +293,8 @@ mcd_status mc_tps_fit(mcd_ctx* ctx, int32_t n_surf, int32_t n_pts, int32_t k, co
  *   system is singular to working precision at that s.
  * Per value one FP64 Cholesky and one triangular inverse (tr(I - A_s) is
  * s |L^{-1}|_F^2); workspace 3 n_pts^2 doubles, in stream order; not for use
- * under stream capture. */
+ * under stream capture.  Like mc_tps_fit, it also uses a stream of its own,
+ * joined to `stream` by events. */
 mcd_status mc_tps_gcv(mcd_ctx* ctx, int32_t n_pts, int32_t k, const double* x, const double* y,
                       int32_t n_s, const double* s_values, double* score, mcd_stream stream);
 
