@@ -53,6 +53,19 @@ def test_fit_matches_oracle(ctx, k, n, s):
     np.testing.assert_allclose(np.hstack([np.ones((n, 1)), x]).T @ coef[:n], 0.0, atol=1e-8)
 
 
+@pytest.mark.parametrize("n", [1, 5, 31, 32, 33, 64, 65, 97])
+def test_fit_at_block_edges(ctx, n):
+    """The projected system has n = n_pts - k - 1 rows, factored in blocks of
+    32 with one block of look-ahead and solved one block per launch: one
+    block only (n <= 32), a last block of one row (33, 65), exact multiples."""
+    k = 2
+    rng = np.random.default_rng(700 + n)
+    x, y = data(rng, n + k + 1, k)
+    _, out = gpu_fit(ctx, [x], [y], 0.05)
+    c_ref, d_ref = tps.fit(x, y, 0.05)
+    np.testing.assert_allclose(out["fitted"].cpu().numpy()[0], tps.evaluate(x, x, c_ref, d_ref), rtol=0, atol=1e-8)
+
+
 def test_several_surfaces_and_paper_size(ctx):
     rng = np.random.default_rng(5)
     xs, ys = [], []
@@ -151,7 +164,7 @@ def test_repeated_points_and_bad_arguments(ctx):
     assert e.value.code == MCD_EINVAL
 
 
-@pytest.mark.parametrize("k,n,lo", [(2, 300, -6), (1, 97, -4), (3, 130, -5), (2, 65, -6)])
+@pytest.mark.parametrize("k,n,lo", [(2, 300, -6), (1, 97, -4), (3, 130, -5), (2, 65, -6), (2, 36, -5)])
 def test_gcv_matches_oracle(ctx, k, n, lo):
     import torch
 
