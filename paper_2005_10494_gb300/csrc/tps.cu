@@ -17,12 +17,17 @@
 // one multi-block launch per 32 rows.  The fitted values at the data are
 // y - s c.
 //
-// Maximiser.  One block per surface: projected BFGS on -f inside a box
-// (Armijo backtracking along the projected path), started at the data point
-// with the largest fitted value inside the box; f and its gradient are block
-// reductions over the N centres.
+// Maximiser.  One thread-block cluster of 8 CTAs per surface: projected
+// BFGS on -f inside a box (Armijo backtracking along the projected path),
+// started at the data point with the largest fitted value inside the box.
+// f and its gradient are sums over the N centres, which the CTAs of the
+// cluster split and combine through distributed shared memory (FP64 runs
+// at about two FMAs per SM clock on this GPU, so one SM per surface left
+// the search bound by that one SM); every CTA then takes the same step.
 #include <cmath>
 #include <cstdint>
+
+#include <cooperative_groups.h>
 
 #include "tps.cuh"
 
@@ -615,38 +620,76 @@ __global__ void __launch_bounds__(1024) gcv_score_kernel(const double* __restric
 
 // ---- maximiser ---------------------------------------------------------------
 constexpr int kMaxThreads = 256;
+constexpr int kArgmaxCluster = 8;    // CTAs per surface (a thread-block cluster)
 
-// f and its gradient at z (all threads return the same values).
+// f and its gradient at z, the same values in every thread of the cluster.
+// CTA `rank` sums the centres rank, rank + C, ... (C = kArgmaxCluster) in its
+// threads; the block's four sums go to its slot part[parity]; after one
+// cluster barrier every CTA adds the C slots, read through distributed
+// shared memory, in rank order, so all CTAs hold bit-identical f and g (and
+// take the same branches of the search).  The slots alternate with the
+// parity of the evaluation, so a CTA that runs ahead writes the other slot
+// while the rest still read this one; it cannot get two evaluations ahead,
+// since each evaluation's barrier waits for every CTA.
 __device__ void f_and_grad(const double* __restrict__ x, const double* __restrict__ coef, int N, int k,
-                           const double* z, double& f, double* g, double* red) {
-    double lf = 0.0, lg[3] = {0.0, 0.0, 0.0};
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+                           const double* z, double& f, double* g, double (*red)[4], double (*part)[4],
+                           int& parity) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = static_cast<int>(cluster.block_rank());
+    double l4[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = rank * blockDim.x + threadIdx.x; i < N; i += kArgmaxCluster * blockDim.x) {
         double diff[3], r2 = 0.0;
         for (int q = 0; q < k; ++q) {
             diff[q] = z[q] - x[static_cast<int64_t>(i) * k + q];
             r2 += diff[q] * diff[q];
         }
         const double r = sqrt(r2), c = coef[i];
-        lf += c * eta(r, k);
+        l4[0] += c * eta(r, k);
         const double fac = c * deta_over_r(r, k);
-        for (int q = 0; q < k; ++q) lg[q] += fac * diff[q];
+        for (int q = 0; q < k; ++q) l4[1 + q] += fac * diff[q];
     }
-    f = block_sum<kMaxThreads>(lf, red) + coef[N];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+        for (int o = 16; o >= 1; o >>= 1) l4[v] += __shfl_xor_sync(0xffffffffu, l4[v], o);
+    if (lane == 0) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) red[warp][v] = l4[v];
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double t = 0.0;
+        for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += red[w][threadIdx.x];
+        part[parity][threadIdx.x] = t;
+    }
+    cluster.sync();
+    double tot[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int r = 0; r < kArgmaxCluster; ++r) {
+        const double* pr = cluster.map_shared_rank(&part[parity][0], r);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) tot[v] += pr[v];
+    }
+    parity ^= 1;
+    f = tot[0] + coef[N];
     for (int q = 0; q < k; ++q) f += coef[N + 1 + q] * z[q];
-    for (int q = 0; q < 3; ++q) g[q] = q < k ? block_sum<kMaxThreads>(lg[q], red) + coef[N + 1 + q] : 0.0;
+    for (int q = 0; q < 3; ++q) g[q] = q < k ? tot[1 + q] + coef[N + 1 + q] : 0.0;
 }
 
-__global__ void __launch_bounds__(kMaxThreads) argmax_tps_kernel(const double* __restrict__ x,
+__global__ void __cluster_dims__(kArgmaxCluster, 1, 1) __launch_bounds__(kMaxThreads)
+argmax_tps_kernel(const double* __restrict__ x,
                                                                  const double* __restrict__ coef,
                                                                  const double* __restrict__ fitted, int N, int k,
                                                                  const double* __restrict__ lo,
                                                                  const double* __restrict__ hi, int iters,
                                                                  double* __restrict__ xbest,
                                                                  double* __restrict__ fbest) {
-    __shared__ double red[kMaxThreads / 32];
+    __shared__ double red[kMaxThreads / 32][4];
+    __shared__ double part[2][4];
     __shared__ double sbest[kMaxThreads];
     __shared__ int sidx[kMaxThreads];
-    const int surf = blockIdx.x;
+    int parity = 0;
+    const int surf = blockIdx.x / kArgmaxCluster;   // one cluster of CTAs per surface
     const double* X = x + static_cast<int64_t>(surf) * N * k;
     const double* C = coef + static_cast<int64_t>(surf) * (N + k + 1);
     const double* F = fitted + static_cast<int64_t>(surf) * N;
@@ -676,7 +719,7 @@ __global__ void __launch_bounds__(kMaxThreads) argmax_tps_kernel(const double* _
     const int start = sidx[0];
     double z[3] = {0, 0, 0}, g[3] = {0, 0, 0}, f;
     for (int q = 0; q < k; ++q) z[q] = start >= 0 ? X[static_cast<int64_t>(start) * k + q] : 0.5 * (lo[q] + hi[q]);
-    f_and_grad(X, C, N, k, z, f, g, red);
+    f_and_grad(X, C, N, k, z, f, g, red, part, parity);
     // inverse-Hessian approximation of -f (ascent direction H g)
     double H[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
     double scale = 0.0;
@@ -708,7 +751,7 @@ __global__ void __launch_bounds__(kMaxThreads) argmax_tps_kernel(const double* _
         bool moved = false;
         for (int ls = 0; ls < 60; ++ls) {
             for (int q = 0; q < k; ++q) zn[q] = fmin(fmax(z[q] + t * p[q], lo[q]), hi[q]);
-            f_and_grad(X, C, N, k, zn, fn, gn, red);
+            f_and_grad(X, C, N, k, zn, fn, gn, red, part, parity);
             double dz = 0.0, gz = 0.0;
             for (int q = 0; q < k; ++q) { dz += fabs(zn[q] - z[q]); gz += g[q] * (zn[q] - z[q]); }
             if (dz == 0.0) break;
@@ -733,10 +776,12 @@ __global__ void __launch_bounds__(kMaxThreads) argmax_tps_kernel(const double* _
         }
         if (df <= 1e-16 * fmax(1.0, fabs(f))) break;
     }
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && cooperative_groups::this_cluster().block_rank() == 0) {
         for (int q = 0; q < k; ++q) xbest[static_cast<int64_t>(surf) * k + q] = z[q];
         fbest[surf] = f;
     }
+    // no CTA leaves while another may still read its partial sums
+    cooperative_groups::this_cluster().sync();
 }
 
 }  // namespace
@@ -895,7 +940,8 @@ cudaError_t tps_gcv(const double* x, const double* y, int N, int k, const double
 cudaError_t tps_argmax(const double* x, const double* coef, const double* fitted, int n_surf, int N, int k,
                        const double* lo, const double* hi, int iters, double* xbest, double* fbest,
                        cudaStream_t stream) {
-    argmax_tps_kernel<<<n_surf, kMaxThreads, 0, stream>>>(x, coef, fitted, N, k, lo, hi, iters, xbest, fbest);
+    argmax_tps_kernel<<<n_surf * kArgmaxCluster, kMaxThreads, 0, stream>>>(x, coef, fitted, N, k, lo, hi, iters, xbest,
+                                                                          fbest);
     return cudaGetLastError();
 }
 
