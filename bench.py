@@ -260,8 +260,10 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true", help="skip the d=10/20, smoothing and C3 lines")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle baseline")
     ap.add_argument("--case", default=None, choices=["c2-small", "c4-small", "c5-small", "smooth", "smooth-f32",
-                                                      "c2-shared", "c2-shared-full"],
-                    help="run a small profiling case (a few launches, no timing) and exit")
+                                                      "c2-shared", "c2-shared-full", "tps", "shared-dims",
+                                                      "perdesign-dims", "tps-timing"],
+                    help="run a small profiling case (a few launches, no timing), or one of the timing sweeps "
+                         "(shared-dims, perdesign-dims, tps-timing: JSON lines), and exit")
     return ap.parse_args()
 
 
@@ -1129,6 +1131,88 @@ def run_extras(pkg, ctx, c2, rates, sm_count):
     return ex
 
 
+def _best_kernel_ms(make_plan, run, reps=3):
+    """Best of `reps` plan launches, the plan's own CUDA-event kernel time."""
+    import torch
+    best, out = float("inf"), None
+    for _ in range(reps):
+        plan = make_plan()
+        out = run(plan)
+        torch.cuda.synchronize()
+        best = min(best, plan.kernel_ms())
+        plan.close()
+    return best, out
+
+
+def run_timing_case(case, pkg, ctx):
+    """Timing sweeps behind the per-dimension layout choices and the spline
+    timings: one JSON line per configuration (CUDA events, best of three)."""
+    import torch
+
+    import workloads
+    if case == "shared-dims":
+        # shared-draw kernel: one LKJ(2) scenario per d with 2048 designs on
+        # one stream (common random numbers), 2e6 draws, h = 1e-2
+        for d in range(1, 21):
+            prob = workloads.crn_groups(np.random.default_rng(d), d_list=[d], group=2048, extra=0,
+                                        n_draws=2_000_000, draw_begin=0)
+            dp = pkg.DeviceProblem.from_workload(prob)
+            line = {"case": case, "d": d, "designs": prob.n_design, "draws": 2_000_000}
+            for grad in (False, True):
+                ms, out = _best_kernel_ms(lambda: pkg.Plan(ctx, dp, grad=grad, timing=True, shared=True),
+                                          lambda plan: plan.grad(3, None, 0.01) if grad else plan.eval(3))
+                line["adj" if grad else "fwd"] = prob.total_draws() / (ms * 1e-3)
+            print(json.dumps(line), flush=True)
+        return
+    if case == "perdesign-dims":
+        # per-design kernel: 64 designs of one AR(1) scenario (rho 0.3) with
+        # their own stream keys, 4e6 draws each
+        for d in range(1, 21):
+            rng = np.random.default_rng(d)
+            J, N = 64, 4_000_000
+            prob = workloads.Problem("dims", [workloads.ar1(d, 0.3)], [0] * J,
+                                     [rng.normal(0.3, 0.3, d) for _ in range(J)], [np.full(d, 2.2) for _ in range(J)],
+                                     [N] * J, np.arange(J) + 5)
+            dp = pkg.DeviceProblem.from_workload(prob)
+            line = {"case": case, "d": d, "designs": J, "draws": N}
+            for grad in (False, True):
+                ms, out = _best_kernel_ms(lambda: pkg.Plan(ctx, dp, grad=grad, timing=True),
+                                          lambda plan: plan.grad(1, None, 0.01) if grad else plan.eval(1))
+                line["adj" if grad else "fwd"] = J * N / (ms * 1e-3)
+            print(json.dumps(line), flush=True)
+        return
+    # tps-timing: the spline fit and its maximiser at the paper's 2000 points
+    # (k = 2, 3) and at 4096 (k = 2), smoothing 0.01 (fit) and 1e-6 (maximiser)
+    for N, k in ((2000, 2), (2000, 3), (4096, 2)):
+        rng = np.random.default_rng(N + k)
+        xs = rng.uniform(0, 1, (1, N, k))
+        x = torch.as_tensor(xs, dtype=torch.float64, device="cuda")
+        y = torch.as_tensor(np.exp(-3.0 * ((xs[0] - 0.55) ** 2).sum(1))[None] + rng.normal(0, 0.01, (1, N)),
+                            dtype=torch.float64, device="cuda")
+        lo = torch.zeros(k, dtype=torch.float64, device="cuda")
+        hi = torch.ones(k, dtype=torch.float64, device="cuda")
+        t_fit, t_max = [], []
+        for rep in range(4):
+            a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            a.record()
+            pkg.mc_tps_fit(ctx, x, y, smoothing=0.01)
+            b.record()
+            fit = pkg.mc_tps_fit(ctx, x, y, smoothing=1e-6)
+            torch.cuda.synchronize()
+            c0 = torch.cuda.Event(enable_timing=True)
+            c0.record()
+            am = pkg.mc_tps_argmax(ctx, x, fit, lo, hi, iters=300)
+            c.record()
+            c.synchronize()
+            if rep > 0:
+                t_fit.append(a.elapsed_time(b))
+                t_max.append(c0.elapsed_time(c))
+        ctx.sync_status()
+        print(json.dumps({"case": case, "points": N, "k": k, "fit_ms": min(t_fit), "argmax_ms": min(t_max),
+                          "argmax_x": am["x"].cpu().numpy().ravel().tolist(), "argmax_f": float(am["f"].item())}),
+              flush=True)
+
+
 def run_case(case):
     """Small cases for profilers: a few launches of one kernel, inputs > L2."""
     import torch
@@ -1136,6 +1220,20 @@ def run_case(case):
     import paper_2005_10494_gb300 as pkg
     import workloads
     ctx = pkg.Context(0)
+    if case in ("shared-dims", "perdesign-dims", "tps-timing"):
+        run_timing_case(case, pkg, ctx)
+        return
+    if case == "tps":
+        # two fits and one maximisation of the paper's 2000-point spline, k = 2
+        rng = np.random.default_rng(2002)
+        x = torch.as_tensor(rng.uniform(0, 1, (1, 2000, 2)), dtype=torch.float64, device="cuda")
+        y = torch.as_tensor(rng.normal(0, 1, (1, 2000)), dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            fit = pkg.mc_tps_fit(ctx, x, y, smoothing=0.01)
+        pkg.mc_tps_argmax(ctx, x, fit, torch.zeros(2, dtype=torch.float64, device="cuda"),
+                          torch.ones(2, dtype=torch.float64, device="cuda"), iters=300)
+        ctx.sync_status()
+        return
     if case in ("smooth", "smooth-f32"):
         S, G = 512, 256                       # FP64: 256 MB in, 256 MB out
         if case == "smooth-f32":
