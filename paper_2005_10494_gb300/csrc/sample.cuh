@@ -50,7 +50,7 @@ template <typename R>
 struct TileShared {
     alignas(16) R L[kMaxPad];        // padded packed lower factor
     alignas(16) R t[kMaxD + 4];      // b - mu
-    alignas(16) float tsc[kMaxD + 4];  // t * log2(e) / h
+    alignas(16) float tsc[kMaxD + 4];  // -t * log2(e) / h (negated, for the FMA y log2(e)/h + tsc)
     uint64_t start;
     uint64_t key;
     uint32_t n;
@@ -109,10 +109,17 @@ __device__ __forceinline__ double lds_one(const double* p) {
     return v;
 }
 
-// sigma((t - y)/h) = 1 / (1 + exp((y - t)/h)).
-__device__ __forceinline__ float smooth_keep(float y, float t, float tsc, float hl2e, double) {
-    const float e = ex2_approx(fmadd(y, hl2e, -tsc));
-    return rcp_approx(1.0f + e);
+// The FP32 adjoint forms the sigmoid factors and the gradient sums two
+// coordinates per packed instruction (one_draw), except at d = 16, 18, 20,
+// whose one-block-per-SM kernels measured 7-11 % slower that way than with
+// each row's factor formed right after its transform (64 designs x 4e6
+// draws; 2-18 % faster at the other d, 20 % on the batched mixed-d kernel).
+template <int D>
+__host__ __device__ constexpr bool packed_adjoint() { return !(D == 16 || D == 18 || D == 20); }
+
+// sigma((t - y)/h) = 1 / (1 + exp((y - t)/h)); ntsc = -t log2(e)/h.
+__device__ __forceinline__ float smooth_keep(float y, float t, float ntsc, float hl2e, double) {
+    return rcp_approx(1.0f + ex2_approx(fmadd(y, hl2e, ntsc)));
 }
 static __device__ __noinline__ double smooth_keep(double y, double t, float, float, double hinv) {
     return 1.0 / (1.0 + exp((y - t) * hinv));
@@ -175,7 +182,7 @@ template <int D, int I, bool GRAD, typename R>
 struct Rows {
     // Walk rows I..D-1: hit test, and the smoothed-indicator factors.
     __device__ __forceinline__ static void run(const TileView<D, R>& v, const R* z, bool& hit,
-                                               R* keep, R& prod) {
+                                               R* keep, R& prod, float* ntsc) {
         constexpr bool VOL = volatile_loads<D, GRAD, R>();
         const R y = row_dot<D, I, VOL, R>(v, z);
         R t;
@@ -192,26 +199,91 @@ struct Rows {
         }
         hit |= (y > t);
         if constexpr (GRAD) {
-            if (v.hl2e != 0.0f) {
+            if constexpr (sizeof(R) == 4 && packed_adjoint<D>()) {
+                keep[I] = y;                                     // the sigmoid is formed in one_draw
+                ntsc[I] = tsc;
+            } else if (v.hl2e != 0.0f) {
                 keep[I] = smooth_keep(y, t, tsc, v.hl2e, v.hinv);
                 prod *= keep[I];
             }
         }
-        if constexpr (I + 1 < D) Rows<D, I + 1, GRAD, R>::run(v, z, hit, keep, prod);
+        if constexpr (I + 1 < D) Rows<D, I + 1, GRAD, R>::run(v, z, hit, keep, prod, ntsc);
     }
 };
 
-// One draw: y = L z, hit = any(y_i > t_i), and the gradient sums.
+// a[i] = fma(s, x[i], a[i]) for i < D.  With PK, two coordinates per packed
+// FMA (pairs (0, 1), (2, 3), ...: x and a then sit in aligned register
+// pairs); each lane rounds exactly as the scalar FMA does.
+template <int D, bool PK>
+__device__ __forceinline__ void axpy(float (&a)[D], float s, const float* x) {
+    if constexpr (PK) {
+        const float2 s2 = make_float2(s, s);
+#pragma unroll
+        for (int i = 0; i + 1 < D; i += 2) {
+            const float2 r = __ffma2_rn(s2, make_float2(x[i], x[i + 1]), make_float2(a[i], a[i + 1]));
+            a[i] = r.x;
+            a[i + 1] = r.y;
+        }
+        if constexpr (D % 2 != 0) a[D - 1] = __fmaf_rn(s, x[D - 1], a[D - 1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < D; ++i) a[i] = __fmaf_rn(s, x[i], a[i]);
+    }
+}
+
+// One draw: y = L z, hit = any(y_i > t_i), and the gradient sums.  In the
+// FP32 adjoint (packed_adjoint) the sigmoid factors and the sums go two
+// coordinates per packed instruction (fma.rn.f32x2 / add.rn.f32x2, rounded
+// lane by lane as the scalar instructions, so the sums are bit-identical):
+// always for the sigmoid and G (arrays of this draw), and for A and B when
+// the draw's normals start at an even index of the group's array (zodd
+// false), so that they pair with the accumulators without register moves.
 template <int D, bool GRAD, bool ALL_VALID, typename R>
-__device__ __forceinline__ void one_draw(const R* z, const TileView<D, R>& v, bool valid,
+__device__ __forceinline__ void one_draw(const R* z, bool zodd, const TileView<D, R>& v, bool valid,
                                          Acc<D, GRAD, R>& acc) {
     bool hit = false;
     R keep[GRAD ? D : 1];
+    float ntsc[GRAD ? D : 1];
     R prod = R(1);
-    Rows<D, 0, GRAD, R>::run(v, z, hit, keep, prod);
+    Rows<D, 0, GRAD, R>::run(v, z, hit, keep, prod, ntsc);
     const bool counted = ALL_VALID ? hit : (hit && valid);
     acc.cnt += counted ? 1u : 0u;
-    if constexpr (GRAD) {
+    if constexpr (GRAD && sizeof(R) == 4 && packed_adjoint<D>()) {
+        const float hv = counted ? 1.0f : 0.0f;
+        const float vv = (ALL_VALID || valid) ? 1.0f : 0.0f;
+        if (!zodd) {
+            axpy<D, true>(acc.A, hv, z);
+            axpy<D, true>(acc.B, vv, z);
+        } else {
+            axpy<D, false>(acc.A, hv, z);
+            axpy<D, false>(acc.B, vv, z);
+        }
+        if (v.hl2e != 0.0f) {
+            // keep_i = 1 / (1 + 2^(y_i log2(e)/h - t_i log2(e)/h)); keep holds y
+            const float2 h2 = make_float2(v.hl2e, v.hl2e), one2 = make_float2(1.0f, 1.0f);
+#pragma unroll
+            for (int i = 0; i + 1 < D; i += 2) {
+                const float2 x = __ffma2_rn(make_float2(keep[i], keep[i + 1]), h2, make_float2(ntsc[i], ntsc[i + 1]));
+                const float2 u = __fadd2_rn(one2, make_float2(ex2_approx(x.x), ex2_approx(x.y)));
+                keep[i] = rcp_approx(u.x);
+                keep[i + 1] = rcp_approx(u.y);
+            }
+            if constexpr (D % 2 != 0)
+                keep[D - 1] = rcp_approx(1.0f + ex2_approx(__fmaf_rn(keep[D - 1], v.hl2e, ntsc[D - 1])));
+#pragma unroll
+            for (int i = 0; i < D; ++i) prod *= keep[i];
+            prod *= vv;
+            const float2 p2 = make_float2(prod, prod), m1 = make_float2(-1.0f, -1.0f);
+#pragma unroll
+            for (int i = 0; i + 1 < D; i += 2) {
+                const float2 omk = __ffma2_rn(make_float2(keep[i], keep[i + 1]), m1, one2);
+                const float2 g = __ffma2_rn(p2, omk, make_float2(acc.G[i], acc.G[i + 1]));
+                acc.G[i] = g.x;
+                acc.G[i + 1] = g.y;
+            }
+            if constexpr (D % 2 != 0) acc.G[D - 1] = __fmaf_rn(prod, 1.0f - keep[D - 1], acc.G[D - 1]);
+        }
+    } else if constexpr (GRAD) {
         const R hv = counted ? R(1) : R(0);
 #pragma unroll
         for (int i = 0; i < D; ++i) acc.A[i] = fmadd(hv, z[i], acc.A[i]);
@@ -252,7 +324,7 @@ __device__ __forceinline__ void group_draws(uint32_t call_lo, uint64_t call, con
             const int last = (g + 1) * D - 1;           // last normal of draw g
             if (last >= 4 * c && last < 4 * c + 4) {
                 const bool valid = ALL_VALID || ((base + g - ofs) < n);
-                one_draw<D, GRAD, ALL_VALID, R>(&z[g * D], v, valid, acc);
+                one_draw<D, GRAD, ALL_VALID, R>(&z[g * D], ((g * D) & 1) != 0, v, valid, acc);
             }
         }
     }
@@ -410,7 +482,7 @@ __device__ __forceinline__ void sample_body(const SampleParams& P) {
             const double tt = P.b[ts.vec_off + i] - P.mu[ts.vec_off + i];
             if (tt != tt) set_status(P.status, MCD_ENAN, ts.design);
             ts.t[i] = static_cast<R>(tt);
-            ts.tsc[i] = P.hinv_log2e != 0.0f ? static_cast<float>(tt) * P.hinv_log2e : 0.0f;
+            ts.tsc[i] = P.hinv_log2e != 0.0f ? -(static_cast<float>(tt) * P.hinv_log2e) : 0.0f;
         }
         __syncthreads();
         if (ts.ok) Dispatch<DLO, DHI, GRAD, R>::run(d, ts, P, cred, gred);
