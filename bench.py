@@ -60,10 +60,34 @@ SHARED_SOURCES = [os.path.join(ROOT, "paper_2005_10494_gb300", "csrc", f)
 #   (lg2, scale, sqrt, angle fma, sin, cos, 2 products) -> 4 per normal;
 #   transform d(d+1)/2 FMA; indicator d compares + 1 count.
 #   Adjoint adds 2d + 1 (likelihood-ratio sums) and 7d (sigmoid factors).
+def packed_adjoint(d):
+    """The FP32 adjoint forms its sigmoid factors and sums two coordinates
+    per packed instruction except at d = 16, 18, 20 (csrc/sample.cuh)."""
+    return d not in (16, 18, 20)
+
+
+def adjoint_fp32_ops(d):
+    """FP32 instructions of the adjoint per draw: scalar and packed (x2).
+    Per coordinate: the sums A and B, the sigmoid argument, 1 + e, 1 - keep
+    and the sum G (6), plus the running product (scalar, d).  Packed, the
+    four sigmoid terms take floor(d/2) packed and d mod 2 scalar
+    instructions each; A and B likewise on the draws whose normals start at
+    an even index of their group (all draws at even d, half at odd d), else
+    d scalar each."""
+    if not packed_adjoint(d):
+        return 7.0 * d, 0.0
+    half, odd = d // 2, d % 2
+    pa = 1.0 if odd == 0 else 0.5
+    scalar = 2 * (pa * odd + (1 - pa) * d) + 4 * odd + d
+    packed = 2 * pa * half + 4 * half
+    return scalar, packed
+
+
 def ops_per_draw(d, grad):
     ops = 16 * d + d * (d + 1) // 2 + d + 1
     if grad:
-        ops += 2 * d + 1 + 7 * d
+        sc, pk = adjoint_fp32_ops(d)
+        ops += 2 * d + 1 + sc + pk
     return ops
 
 
@@ -89,7 +113,9 @@ def fp32_flops_per_draw(d, grad):
 #     share the loads) and t stays in registers;
 #   indicator: d compares and one count add (ALU).
 #   Adjoint per coordinate: 7 FP32 (sums A and B; sigmoid argument, 1 + e,
-#     running product, 1 - keep, sum G), ex2, rcp and, above d = 6, one
+#     running product, 1 - keep, sum G; all but the product two coordinates
+#     per packed instruction where packed_adjoint, see adjoint_fp32_ops),
+#     ex2, rcp and, above d = 6, one
 #     shared load (the scaled threshold); one select per draw (ALU).  At the
 #     dimensions where the adjoint reloads with volatile loads, every draw
 #     loads all chunks of L and both thresholds.
@@ -112,8 +138,8 @@ def hbm_peak(path=os.path.join(ROOT, "MEASURED_PEAKS.json")):
 def class_counts(d, grad):
     calls, pairs = d / 4.0, d / 2.0
     c = {"mul_wide": 19 * calls, "alu": 20 * calls + 4 * pairs + d + 1,
-         "ffma": 6 * pairs + d * (d + 1) / 2.0, "lg2": pairs, "sqrt": pairs, "sin": pairs, "cos": pairs,
-         "ex2": 0.0, "rcp": 0.0, "lds128": 0.0}
+         "ffma": 6 * pairs + d * (d + 1) / 2.0, "ffma2": 0.0, "lg2": pairs, "sqrt": pairs, "sin": pairs,
+         "cos": pairs, "ex2": 0.0, "rcp": 0.0, "lds128": 0.0}
     # adjoint kernels that reload the factor (and both thresholds) for
     # every draw: the dimensions of volatile_loads() in sample.cuh
     reload = grad and (8 <= d <= 12 or 15 <= d <= 19)
@@ -121,7 +147,9 @@ def class_counts(d, grad):
         group = 1 if (d % 4 == 0 or reload) else (2 if d % 2 == 0 else 4)
         c["lds128"] = sum((i + 4) // 4 for i in range(d)) / float(group)
     if grad:
-        c["ffma"] += 7 * d
+        sc, pk = adjoint_fp32_ops(d)
+        c["ffma"] += sc
+        c["ffma2"] += pk
         c["ex2"] += d
         c["rcp"] += d
         c["alu"] += 1
@@ -233,14 +261,15 @@ def pipe_bound(rates, d, grad, sm_count, mhz=SM_MAX_MHZ):
     per clock per scheduler (128 operations per SM clock)."""
     n = class_counts(d, grad)
     half = rates["ffma"] / 2.0
+    r_pk = rates.get("ffma2", rates["ffma"] / 2.0)
     # wide multiplies: the faster of the bare multiply-add and the multiplies
     # inside Philox rounds as the kernels run them
     r_mul = max(rates["mul_wide"], rates.get("philox", 0.0))
     clk = {
         "int_multiply": n["mul_wide"] / r_mul,
         "alu": n["alu"] / rates["lop3"],
-        "fp32": n["ffma"] / rates["ffma"],
-        "fma_pipes": (n["mul_wide"] * half / r_mul + n["ffma"]) / rates["ffma"],
+        "fp32": n["ffma"] / rates["ffma"] + n["ffma2"] / r_pk,
+        "fma_pipes": (n["mul_wide"] * half / r_mul + n["ffma"]) / rates["ffma"] + n["ffma2"] / r_pk,
         "mufu": sum(n[k] / rates[k] for k in MUFU),
         "lsu": n["lds128"] / rates["lds128"],
         "issue": sum(n.values()) / LANES,

@@ -19,10 +19,28 @@ def test_class_counts_d3():
         assert f[k] == pytest.approx(1.5)
     assert f["ex2"] == f["rcp"] == f["lds128"] == 0
     g = bench.class_counts(3, True)
-    assert g["ffma"] == pytest.approx(15 + 21)
+    # adjoint FP32 (packed form, d odd): A and B packed on half the draws
+    # (1 packed + 1 scalar) and scalar on the other half (3 each); the four
+    # sigmoid terms 1 packed + 1 scalar each; the running product 3
+    assert g["ffma"] == pytest.approx(15 + 2 * (0.5 + 1.5) + 4 + 3)
+    assert g["ffma2"] == pytest.approx(2 * 0.5 + 4)
     assert g["ex2"] == g["rcp"] == 3
     assert g["alu"] == pytest.approx(26)
-    assert sum(g.values()) == pytest.approx(88.25)
+    assert sum(g.values()) == pytest.approx(83.25)
+    assert bench.ops_per_draw(3, True) == pytest.approx(81)
+
+
+@pytest.mark.parametrize("d,scalar,packed", [
+    (3, 11, 5),
+    (4, 4, 2 * 2 + 4 * 2),       # even d: A and B packed on every draw
+    (10, 10, 2 * 5 + 4 * 5),
+    (16, 7 * 16, 0),             # the scalar form at d = 16, 18, 20
+    (20, 7 * 20, 0),
+])
+def test_adjoint_fp32_ops(d, scalar, packed):
+    sc, pk = bench.adjoint_fp32_ops(d)
+    assert sc == pytest.approx(scalar) and pk == pytest.approx(packed)
+    assert sc + 2 * pk == pytest.approx(7 * d)   # a packed instruction does two coordinates' work
 
 
 @pytest.mark.parametrize("d,grad,lds", [
@@ -49,8 +67,15 @@ def test_pipe_bound_picks_the_busiest_pipe():
     assert b["sm_clk_per_draw"]["mufu"] == pytest.approx(mufu)
     # the wide multiplies take the faster of the two measured rates
     assert b["sm_clk_per_draw"]["int_multiply"] == pytest.approx(n["mul_wide"] / 30.0)
-    assert b["binding"] == "issue"
-    assert b["bound_draw_evals_per_s"] == pytest.approx(152 * 2000e6 / issue)
+    # the busiest pipe binds; with the adjoint's packed FP32 work, MUFU (9
+    # ops at 16 per clock, 3 at 32) is within 1 % of issue at d=3
+    clk = b["sm_clk_per_draw"]
+    assert b["binding"] == max(clk, key=clk.get) == "mufu"
+    assert b["bound_draw_evals_per_s"] == pytest.approx(152 * 2000e6 / mufu)
+    fast = dict(rates, lg2=64.0, sqrt=64.0, sin=64.0, cos=64.0, rcp=64.0, ex2=64.0)
+    bf = bench.pipe_bound(fast, 3, True, 152, mhz=2000.0)
+    assert bf["binding"] == "issue"
+    assert bf["bound_draw_evals_per_s"] == pytest.approx(152 * 2000e6 / issue)
     slow = dict(rates, sin=2.0)
     b2 = bench.pipe_bound(slow, 3, True, 152, mhz=2000.0)
     assert b2["binding"] == "mufu"
