@@ -28,9 +28,11 @@ constexpr int kRowsPerBlock = 32;     // output rows of one block (2-D)
 constexpr int kColsPerBlock = 128;    // output columns of one block (2-D)
 constexpr int kLine = 512;            // outputs of one block (1-D)
 // The interior class's FP32 stencil is also stored compactly after the class
-// table, 16-byte aligned, for vector loads (kIntSlot floats, T*T used).
+// table, 16-byte aligned, for vector loads (T*T of the first 64 floats),
+// followed at kSepOff by its separable factors (see weights_kernel).
 constexpr int kClassSlots = (kMaxReach + 1) * (kMaxReach + 1) * (kMaxReach + 1) * (kMaxReach + 1);
-constexpr int kIntSlot = 64;
+constexpr int kSepOff = 64;
+constexpr int kIntSlot = kSepOff + 16;
 
 __host__ __device__ inline int reach_of(double bw) {
     const double f = floor(bw);
@@ -117,6 +119,24 @@ __global__ void weights_kernel(int R, double bw, int degree, bool two_d, int gx,
             w[q] = W * s;
             wf[q] = static_cast<float>(W * s);
             if (wint) wint[q] = wf[q];
+        }
+    }
+    // The interior stencil in 2-D is separable into two rank-one parts.  With
+    // symmetric product weights W(dx) W(dy), the coefficients of the odd
+    // monomials (dx, dy, dx dy) vanish, so the stencil is
+    //   W(dx) W(dy) (u_0 + u_x dx^2 + u_y dy^2)
+    //     = [W(dx) (u_0 + u_x dx^2)] W(dy) + [W(dx) u_y] dy^2 W(dy).
+    // The tile kernel applies it as two row filters (W(v), v^2 W(v)) and one
+    // column pass with the weights W(u) (u_0 + u_x u^2) and W(u) u_y; for
+    // degree 0 and 1, u_x = u_y = 0 (one rank-one part).
+    if (wint && two_d) {
+        const double ux = nb == 6 ? u[3] : 0.0, uy = nb == 6 ? u[5] : 0.0;
+        for (int k = 0; k <= R; ++k) {
+            const double wk = tricube(k / bw);
+            wint[kSepOff + k] = static_cast<float>(wk);
+            wint[kSepOff + 4 + k] = static_cast<float>(k * k * wk);
+            wint[kSepOff + 8 + k] = static_cast<float>(wk * (u[0] + ux * k * k));
+            wint[kSepOff + 12 + k] = static_cast<float>(wk * uy);
         }
     }
 }
@@ -438,22 +458,28 @@ __device__ __forceinline__ void tile_outputs(float (*tile)[Tile2D<R>::SCP], int 
     // (visited in row-major order, so a tie keeps the lowest index)
     float best = -INFINITY;
     int bsel = -1;
-    // Interior stencil of every output of the patch.  The interior window is
-    // symmetric (tricube product weights, monomial basis), so its stencil
-    // depends only on (|u|, |v|) sorted: (R+1)(R+2)/2 distinct weights, read
-    // at the canonical positions (R + a, R + b), a <= b.
+    // Interior stencil of every output of the patch, in its separable form
+    // (weights_kernel): for each of the 4 + 2R window rows, the two row
+    // filters H1 = sum_v W(v) x_(c+v) and H2 = sum_v v^2 W(v) x_(c+v) at the
+    // patch's 4 columns, then every output row within reach adds
+    // p(u) H1 + q(u) H2.  Adjacent columns go two per packed FP32
+    // instruction: the window row's values sit in aligned register pairs
+    // (16-byte shared loads), so a pair of symmetric taps whose first index
+    // is even is one packed add, otherwise two scalar adds.
     float acc[4][4];
     {
-        constexpr int NC = (R + 1) * (R + 2) / 2;
-        float wc[NC];
+        const float* sep = wint + kSepOff;
+        float hw[R + 1], ha[R + 1], vp[R + 1], vq[R + 1];
 #pragma unroll
-        for (int a = 0, n = 0; a <= R; ++a)
+        for (int k = 0; k <= R; ++k) {
+            hw[k] = __ldg(sep + k);
+            ha[k] = __ldg(sep + 4 + k);
+            vp[k] = __ldg(sep + 8 + k);
+            vq[k] = __ldg(sep + 12 + k);
+        }
+        float2 accp[4][2];
 #pragma unroll
-            for (int b = a; b <= R; ++b, ++n) wc[n] = __ldg(&wint[(R + a) * T + (R + b)]);
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+        for (int i = 0; i < 4; ++i) accp[i][0] = accp[i][1] = make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int ir = 0; ir < 4 + 2 * R; ++ir) {
             float in[4 * NV];
@@ -463,21 +489,43 @@ __device__ __forceinline__ void tile_outputs(float (*tile)[Tile2D<R>::SCP], int 
                 const float4 q = src[v];
                 in[4 * v] = q.x; in[4 * v + 1] = q.y; in[4 * v + 2] = q.z; in[4 * v + 3] = q.w;
             }
+            float2 h1[2], h2[2];
+#pragma unroll
+            for (int jp = 0; jp < 2; ++jp) {
+                const int j = 2 * jp;
+                float2 a1 = __fmul2_rn(make_float2(hw[0], hw[0]), make_float2(in[j + R], in[j + R + 1]));
+                float2 a2 = make_float2(0.0f, 0.0f);
+#pragma unroll
+                for (int k = 1; k <= R; ++k) {
+                    float2 sk;
+                    if ((j + R - k) % 2 == 0) {
+                        sk = __fadd2_rn(make_float2(in[j + R - k], in[j + R - k + 1]),
+                                        make_float2(in[j + R + k], in[j + R + k + 1]));
+                    } else {
+                        sk = make_float2(in[j + R - k] + in[j + R + k], in[j + R - k + 1] + in[j + R + k + 1]);
+                    }
+                    a1 = __ffma2_rn(make_float2(hw[k], hw[k]), sk, a1);
+                    a2 = k == 1 ? __fmul2_rn(make_float2(ha[k], ha[k]), sk)
+                                : __ffma2_rn(make_float2(ha[k], ha[k]), sk, a2);
+                }
+                h1[jp] = a1;
+                h2[jp] = a2;
+            }
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int dx = ir - i;                      // window row of output row i
                 if (dx < 0 || dx >= T) continue;
+                const int u = dx < R ? R - dx : dx - R;
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-#pragma unroll
-                    for (int dy = 0; dy < T; ++dy) {
-                        const int u = dx < R ? R - dx : dx - R, v = dy < R ? R - dy : dy - R;
-                        const int a = u < v ? u : v, b = u < v ? v : u;
-                        // canonical index of (a, b): rows a' < a hold R + 1 - a' entries
-                        const int n = a * (R + 1) - a * (a - 1) / 2 + (b - a);
-                        acc[i][j] = fmaf(wc[n], in[j + dy], acc[i][j]);
-                    }
+                for (int jp = 0; jp < 2; ++jp)
+                    accp[i][jp] = __ffma2_rn(make_float2(vp[u], vp[u]), h1[jp],
+                                             __ffma2_rn(make_float2(vq[u], vq[u]), h2[jp], accp[i][jp]));
             }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            acc[i][0] = accp[i][0].x; acc[i][1] = accp[i][0].y;
+            acc[i][2] = accp[i][1].x; acc[i][3] = accp[i][1].y;
         }
     }
     {
