@@ -116,6 +116,33 @@ def test_argmax_matches_oracle(ctx, k):
         assert np.max(np.abs(tps.gradient(xg, x, c_ref, d_ref))) < 1e-5
 
 
+def test_argmax_of_several_surfaces(ctx):
+    """Each surface is maximised by its own thread-block cluster: four
+    surfaces of different peaks in one call, each against the oracle's
+    maximiser of its own fit."""
+    import torch
+
+    import paper_2005_10494_gb300 as pkg
+    rng = np.random.default_rng(77)
+    xs, ys, peaks = [], [], [(0.3, 0.7), (0.6, 0.4), (0.5, 0.5), (0.8, 0.2)]
+    for pk in peaks:
+        x = rng.uniform(0, 1, (250, 2))
+        y = np.exp(-4.0 * ((x - np.array(pk)) ** 2).sum(1)) + rng.normal(0, 0.01, 250)
+        xs.append(x)
+        ys.append(y)
+    xt, out = gpu_fit(ctx, xs, ys, 0.05)
+    lo = torch.zeros(2, dtype=torch.float64, device="cuda")
+    hi = torch.ones(2, dtype=torch.float64, device="cuda")
+    res = pkg.mc_tps_argmax(ctx, xt, out, lo, hi, iters=300)
+    ctx.sync_status()
+    xg, fg = res["x"].cpu().numpy(), res["f"].cpu().numpy()
+    for q in range(len(peaks)):
+        c_ref, d_ref = tps.fit(xs[q], ys[q], 0.05)
+        xr, fr = tps.argmax(xs[q], c_ref, d_ref, np.zeros(2), np.ones(2))
+        assert fg[q] == pytest.approx(fr, abs=1e-9)
+        np.testing.assert_allclose(xg[q], xr, atol=2e-4)
+
+
 def test_argmax_on_the_box_boundary(ctx):
     import torch
 
