@@ -277,9 +277,12 @@ mcd_status mc_fwer_calibrate(mcd_ctx* ctx, const mcd_problem* prob, const double
  * definite after the projection (repeated points with smoothing 0) gives NaN
  * outputs for that surface and MCD_ENOTSPD with its index at mcd_sync_status.
  * Workspace n_pts^2 doubles, allocated and freed in stream order; not for use
- * under stream capture.  The factorisation also runs kernels on a stream of
- * its own, joined to `stream` by events, so all of the call's work is done
- * when the work queued on `stream` is. */
+ * under stream capture.  Several surfaces are fitted at once on up to four
+ * worker streams, each with its own workspace (the workspace above per
+ * worker, at most about 4 GB in all), and the factorisation also runs
+ * kernels on a stream of its own; all of these are joined to `stream` by
+ * events, so all of the call's work is done when the work queued on
+ * `stream` is. */
 mcd_status mc_tps_fit(mcd_ctx* ctx, int32_t n_surf, int32_t n_pts, int32_t k, const double* x,
                       const double* y, double smoothing, double* coef, double* fitted, mcd_stream stream);
 

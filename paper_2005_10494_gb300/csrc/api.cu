@@ -300,9 +300,9 @@ mcd_status plan_build(mcd_ctx* ctx, const mcd_problem* pr, int32_t flags, int32_
     std::vector<int> present(MCD_MAX_D + 1, 0);
     for (int j = 0; j < J; ++j)
         if (!is_shared[j]) present[scen_d[pr->design_scen[j]]] = 1;
-    int n_small = 0, small_lo = MCD_MAX_D + 1, small_hi = 0;
+    int n_small = 0, small_lo = MCD_MAX_D + 1;
     for (int d = 1; d <= kMixedMaxD; ++d)
-        if (present[d]) { ++n_small; small_lo = std::min(small_lo, d); small_hi = d; }
+        if (present[d]) { ++n_small; small_lo = std::min(small_lo, d); }
     if (pl->fp64) {
         int n_present = 0;
         for (int d = 1; d <= MCD_MAX_D; ++d) n_present += present[d];
@@ -1084,19 +1084,58 @@ mcd_status mc_tps_fit(mcd_ctx* ctx, int32_t n_surf, int32_t n_pts, int32_t k, co
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     MCD_CUDA(cudaStreamIsCapturing(s, &cs), "cudaStreamIsCapturing");
     if (cs != cudaStreamCaptureStatusNone) return fail(ctx, MCD_EINVAL, "mc_tps_fit cannot be captured");
+    // Surfaces are independent fits whose time is mostly dependent chains
+    // (pivots, triangular solves), so up to kTpsWorkers of them run at once,
+    // each worker stream fitting its share in turn with a workspace of its
+    // own; the workers start after the work already queued on `s` and `s`
+    // waits for all of them.  The number of workers is also held to about
+    // 4 GB of workspace.
+    constexpr int kTpsWorkers = 4;
     const size_t nws = tps_workspace_doubles(n_pts, k);
+    const size_t per_worker = nws + 2;
+    int workers = n_surf < kTpsWorkers ? n_surf : kTpsWorkers;
+    while (workers > 1 && per_worker * sizeof(double) * workers > (static_cast<size_t>(4) << 30)) --workers;
     double* ws = nullptr;
-    MCD_CUDA(cudaMallocAsync(&ws, sizeof(double) * (nws + 2), s), "spline workspace");
-    int* bad = reinterpret_cast<int*>(ws + nws);
-    unsigned long long* amax = reinterpret_cast<unsigned long long*>(ws + nws + 1);
+    MCD_CUDA(cudaMallocAsync(&ws, sizeof(double) * per_worker * workers, s), "spline workspace");
     mcd_status rc = MCD_OK;
     const int64_t m = k + 1;
+    cudaStream_t wstream[kTpsWorkers] = {};
+    cudaEvent_t ev_start = nullptr, ev_done[kTpsWorkers] = {};
+    cudaError_t e = cudaSuccess;
+    if (workers > 1) {
+        e = cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming);
+        for (int w = 0; w < workers && e == cudaSuccess; ++w) {
+            e = cudaStreamCreateWithFlags(&wstream[w], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_done[w], cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ev_start, s);
+        for (int w = 0; w < workers && e == cudaSuccess; ++w) e = cudaStreamWaitEvent(wstream[w], ev_start, 0);
+    } else {
+        wstream[0] = s;
+    }
+    if (e != cudaSuccess) rc = cuda_fail(ctx, e, "spline streams");
     for (int q = 0; q < n_surf && rc == MCD_OK; ++q) {
-        cudaError_t e = tps_fit_one(x + static_cast<int64_t>(q) * n_pts * k, y + static_cast<int64_t>(q) * n_pts,
-                                    n_pts, k, smoothing, coef + static_cast<int64_t>(q) * (n_pts + m),
-                                    fitted ? fitted + static_cast<int64_t>(q) * n_pts : nullptr, ws, bad, amax,
-                                    ctx->d_status, q, s);
+        const int w = q % workers;
+        double* wsw = ws + per_worker * w;
+        int* bad = reinterpret_cast<int*>(wsw + nws);
+        unsigned long long* amax = reinterpret_cast<unsigned long long*>(wsw + nws + 1);
+        e = tps_fit_one(x + static_cast<int64_t>(q) * n_pts * k, y + static_cast<int64_t>(q) * n_pts, n_pts, k,
+                        smoothing, coef + static_cast<int64_t>(q) * (n_pts + m),
+                        fitted ? fitted + static_cast<int64_t>(q) * n_pts : nullptr, wsw, bad, amax, ctx->d_status, q,
+                        wstream[w]);
         if (e != cudaSuccess) rc = cuda_fail(ctx, e, "spline launch");
+    }
+    if (workers > 1) {
+        // join every worker that was created, whatever happened above
+        for (int w = 0; w < workers; ++w) {
+            if (wstream[w] && ev_done[w] && cudaEventRecord(ev_done[w], wstream[w]) == cudaSuccess)
+                cudaStreamWaitEvent(s, ev_done[w], 0);
+        }
+        for (int w = 0; w < workers; ++w) {
+            if (ev_done[w]) cudaEventDestroy(ev_done[w]);
+            if (wstream[w]) cudaStreamDestroy(wstream[w]);
+        }
+        if (ev_start) cudaEventDestroy(ev_start);
     }
     cudaFreeAsync(ws, s);
     return rc;

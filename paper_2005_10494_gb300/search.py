@@ -93,6 +93,34 @@ def _dev(a, device):
     return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), dtype=torch.float64, device=device)
 
 
+def _alpha_estimates(ctx, cond, r, n3, n_draws, seed, rounds, u=None):
+    """The noisy expected power of the N3 alpha splits of one r (the first
+    half of optimise_alpha): box points u, each split's scale calibrated to
+    the FWER on the device (n_draws per round, one stream for all splits),
+    then its power under the prior-folded alternative (n_draws, one stream).
+    Returns u (host), the points x (device, [1][N3][n-1]), p_hat (device)
+    and the plan, which the caller closes once the queued work is done."""
+    import torch
+
+    import workloads
+    n = r.shape[0]
+    m, C, Sig0 = workloads.paper_law(cond, r)
+    if u is None:
+        u = workloads.box_points(n3, n - 1, seed)
+    w = workloads.split_from_box(u)
+    N3 = w.shape[0]
+    dev = torch.device("cuda", ctx.device)
+    zeros = _dev(np.zeros(N3 * n), dev)
+    null = binding.DeviceProblem([n], np.zeros(N3), np.full(N3, n_draws), np.zeros(N3), _dev(Sig0.ravel(), dev),
+                                 zeros, zeros)
+    cal = binding.mc_fwer_calibrate(ctx, null, _dev(w.ravel(), dev), workloads.ALPHA0, rounds=rounds, seed=seed)
+    alt = binding.DeviceProblem([n], np.zeros(N3), np.full(N3, n_draws), np.ones(N3), _dev(C.ravel(), dev),
+                                _dev(np.tile(m, N3), dev), cal["b"])
+    plan = binding.Plan(ctx, alt, shared=True)
+    p_hat = plan.eval(seed + 1)["p"]
+    return u, _dev(u, dev).reshape(1, N3, n - 1), p_hat, plan
+
+
 def optimise_alpha(ctx, cond, r, n3=2000, n_draws=10_000_000, seed=0, smoothing=1e-6, rounds=8,
                    final_draws=100_000_000, u=None):
     """Maximise the expected power over the alpha allocations of condition
@@ -117,21 +145,10 @@ def optimise_alpha(ctx, cond, r, n3=2000, n_draws=10_000_000, seed=0, smoothing=
     import workloads
     r = np.asarray(r, dtype=np.float64)
     n = r.shape[0]
-    m, C, Sig0 = workloads.paper_law(cond, r)
-    if u is None:
-        u = workloads.box_points(n3, n - 1, seed)
-    w = workloads.split_from_box(u)
-    N3 = w.shape[0]
     dev = torch.device("cuda", ctx.device)
-    zeros = _dev(np.zeros(N3 * n), dev)
-    null = binding.DeviceProblem([n], np.zeros(N3), np.full(N3, n_draws), np.zeros(N3), _dev(Sig0.ravel(), dev),
-                                 zeros, zeros)
-    cal = binding.mc_fwer_calibrate(ctx, null, _dev(w.ravel(), dev), workloads.ALPHA0, rounds=rounds, seed=seed)
-    alt = binding.DeviceProblem([n], np.zeros(N3), np.full(N3, n_draws), np.ones(N3), _dev(C.ravel(), dev),
-                                _dev(np.tile(m, N3), dev), cal["b"])
-    plan = binding.Plan(ctx, alt, shared=True)
-    p_hat = plan.eval(seed + 1)["p"]
-    x = _dev(u, dev).reshape(1, N3, n - 1)
+    u, x, p_hat, plan = _alpha_estimates(ctx, cond, r, n3, n_draws, seed, rounds, u)
+    N3 = u.shape[0]
+    Sig0 = workloads.paper_law(cond, r)[2]
     if isinstance(smoothing, str):
         grid = np.logspace(-10, -2, 17)
         score = binding.mc_tps_gcv(ctx, x[0], p_hat, grid).cpu().numpy()
@@ -194,10 +211,31 @@ def optimise_design(ctx, cond, r_pairs=None, n3=2000, n_draws=10_000_000, seed=0
     import workloads
     pairs = workloads.paper_r_pairs() if r_pairs is None else r_pairs
     per_r = []
-    for q, (r2, r3) in enumerate(pairs):
-        res = optimise_alpha(ctx, cond, (1.0, r2, r3), n3=n3, n_draws=n_draws, seed=seed + 7 * q,
-                             smoothing=smoothing, final_draws=0)
-        per_r.append((r2, r3, res["p_fit"]))
+    if isinstance(smoothing, str):
+        for q, (r2, r3) in enumerate(pairs):
+            res = optimise_alpha(ctx, cond, (1.0, r2, r3), n3=n3, n_draws=n_draws, seed=seed + 7 * q,
+                                 smoothing=smoothing, final_draws=0)
+            per_r.append((r2, r3, res["p_fit"]))
+    else:
+        # the same per-pair estimates as optimise_alpha, then the splines of
+        # all pairs fitted in one call (independent fits run concurrently)
+        # and maximised in one call (one cluster per surface)
+        xs, ps, plans = [], [], []
+        for q, (r2, r3) in enumerate(pairs):
+            _, xq, pq, plq = _alpha_estimates(ctx, cond, np.array([1.0, r2, r3]), n3, n_draws, seed + 7 * q, 8)
+            xs.append(xq[0])
+            ps.append(pq)
+            plans.append(plq)
+        dev0 = torch.device("cuda", ctx.device)
+        xa = torch.stack(xs)
+        fits = binding.mc_tps_fit(ctx, xa, torch.stack(ps), smoothing=smoothing)
+        k = xa.shape[2]
+        am = binding.mc_tps_argmax(ctx, xa, fits, _dev(np.zeros(k), dev0), _dev(np.ones(k), dev0), iters=300)
+        ctx.sync_status()
+        for plq in plans:
+            plq.close()
+        f = am["f"].cpu().numpy()
+        per_r = [(r2, r3, float(f[q])) for q, (r2, r3) in enumerate(pairs)]
     dev = torch.device("cuda", ctx.device)
     pts, vals, lo_np, hi_np = r_search_box(per_r)
     x = _dev(pts, dev).reshape(1, len(per_r), 2)
