@@ -80,6 +80,22 @@ def test_several_surfaces_and_paper_size(ctx):
                                    rtol=0, atol=1e-8)
 
 
+def test_many_surfaces_on_worker_streams(ctx):
+    """Nine surfaces in one call: up to four worker streams fit two or three
+    surfaces each in turn, each surface against its own oracle fit."""
+    rng = np.random.default_rng(91)
+    xs, ys = [], []
+    for q in range(9):
+        x, y = data(rng, 180 + 7 * q, 2, noise=0.02)
+        xs.append(x[:180])
+        ys.append(y[:180])
+    _, out = gpu_fit(ctx, xs, ys, 0.02)
+    fitted = out["fitted"].cpu().numpy()
+    for q in range(9):
+        c_ref, d_ref = tps.fit(xs[q], ys[q], 0.02)
+        np.testing.assert_allclose(fitted[q], tps.evaluate(xs[q], xs[q], c_ref, d_ref), rtol=0, atol=1e-8)
+
+
 def test_grid_of_4096_points(ctx):
     # the 64 x 64 design grid of one scenario as scattered points
     g = np.linspace(0.05, 0.95, 64)
